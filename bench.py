@@ -1,0 +1,409 @@
+"""Throughput benchmark of the GB300 PIC step.
+
+Workload (default): the large uniform thermal plasma, 2048 x 2048 cells,
+dx = dy = 0.1, dt = 0.07, periodic, electrons + positrons at 8x8 particles
+per cell each (536,870,912 particles), u_th = 0.1, FP32 (--precision fp64
+for the all-FP64 form).  One step = push+deposit, Yee, tile migration and
+end-of-step bookkeeping for every particle and cell.
+
+Printed (rank 0, one JSON line): particle-steps/s of the whole job (inputs
+resident in HBM, CUDA events on the library's stream), the e2e figure
+through the C ABI with host buffers (particles uploaded from pinned host
+memory, stepped, energies and particles read back, all inside the timed
+region), the roofline of the dominant kernel (push_deposit) against the
+measured HBM copy bandwidth, and the FP64 CPU oracle timed on a bounded
+sample on this host as a baseline.
+
+--impl reference times the oracle itself as the reference arm.
+Multi-GPU (torchrun): every rank advances its own independent replica
+(different generator stream); value = all ranks' particle-steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.txt")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--ppc", type=int, default=8, help="particles per cell "
+                    "per side and species")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=512,
+                    help="cells per side of the oracle sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- dist ----
+
+def dist_init(n):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def all_max(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def all_sum(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ------------------------------------------------------------ helpers ----
+
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def push_kernel_hash():
+    src = os.path.join(ROOT, "paper_2106_12485_gb300", "csrc", "k_push.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(precision, n_particles, n_cells):
+    """DRAM bytes per push_deposit launch from the committed ncu summary,
+    scaled to this launch by particles (null if the kernel changed)."""
+    try:
+        with open(TRAFFIC_PATH) as f:
+            for ln in f:
+                if not ln.startswith("push_deposit "):
+                    continue
+                kv = dict(t.split("=", 1) for t in ln.split()[1:])
+                if kv.get("sha") != push_kernel_hash():
+                    return None
+                if kv.get("precision") != precision:
+                    continue
+                bpp = float(kv["dram_bytes_per_particle"])
+                return bpp * n_particles
+    except Exception:
+        return None
+    return None
+
+
+def algorithmic_bytes(n_particles, n_cells, real_bytes):
+    # one read + one write of the SoA record (int32 ix, iy + 5 reals) per
+    # particle, plus E, B read and J written once per cell
+    rec = 8 + 5 * real_bytes
+    return 2 * rec * n_particles + (6 + 3) * real_bytes * n_cells
+
+
+# ---------------------------------------------------------- CPU oracle ----
+
+def oracle_sample(cells, ppc, steps, nthreads):
+    """Times the FP64 oracle on a cells x cells periodic box of the same
+    plasma (both species, same ppc and u_th).  Returns (ps/s, n_particles,
+    seconds)."""
+    from oracle import oracle as O
+    from synthetic import plasma as P
+    sps = []
+    for s, qm in enumerate((-1.0, 1.0)):
+        ld = P.plasma_load(cells, cells, ppc, ppc, species=s,
+                           u_th=(0.1, 0.1, 0.1), dtype=np.float64)
+        sps.append(O.Species(qm, (1 if qm > 0 else -1) / ppc ** 2, ld["ix"],
+                             ld["iy"], ld["x"], ld["y"], ld["ux"], ld["uy"],
+                             ld["uz"], w=ld["w"], ids=ld["id"]))
+    sim = O.Sim(cells, cells, 0.1, 0.1, 0.07, species=sps)
+    n = sum(s.n for s in sps)
+    sim.step(1, nthreads=nthreads)     # warm-up (page faults, threads)
+    t0 = time.perf_counter()
+    sim.step(steps, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return n * steps / dt, n, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    nthreads = os.cpu_count() or 1
+    cells = args.cpu_sample // 2
+    from oracle import oracle as O
+    from synthetic import plasma as P
+    sps = []
+    for s, qm in enumerate((-1.0, 1.0)):
+        ld = P.plasma_load(cells, cells, args.ppc, args.ppc, species=s,
+                           u_th=(0.1, 0.1, 0.1), dtype=np.float64)
+        sps.append(O.Species(qm, (1 if qm > 0 else -1) / args.ppc ** 2,
+                             ld["ix"], ld["iy"], ld["x"], ld["y"], ld["ux"],
+                             ld["uy"], ld["uz"], w=ld["w"], ids=ld["id"]))
+    sim = O.Sim(cells, cells, 0.1, 0.1, 0.07, species=sps)
+    n = sum(s.n for s in sps)
+    for _ in range(args.warmup):
+        sim.step(1, nthreads=nthreads)
+    t0 = time.perf_counter()
+    sim.step(args.steps, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    sample = ("%dx%d periodic box of the same plasma (%d particles), %d "
+              "oracle steps" % (cells, cells, n, args.steps))
+    print(json.dumps({
+        "impl": "reference", "metric": "particle-steps/s", "value": v,
+        "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": v, "unit": "particle-steps/s",
+                         "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def workload_config(args):
+    ppc = args.ppc
+    return {"workload": "uniform thermal plasma %dx%d, e-/e+ %dx%d ppc each, "
+                        "u_th 0.1, dx=dy=0.1, dt=0.07, periodic" %
+                        (args.nx, args.ny, ppc, ppc),
+            "nx": args.nx, "ny": args.ny, "species": 2,
+            "ppc_per_species": ppc * ppc,
+            "particles": 2 * args.nx * args.ny * ppc * ppc,
+            "precision": args.precision,
+            "l2": "inputs larger than L2 (particle store >> 129 MB)"}
+
+
+# --------------------------------------------------------------- main ----
+
+def main():
+    args = parse_args()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    from paper_2106_12485_gb300 import workloads as W
+    from paper_2106_12485_gb300 import zpic as Z
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    prec = Z.FP64 if args.precision == "fp64" else Z.FP32
+    rb = 8 if prec == Z.FP64 else 4
+    cfg = W.precision_study(args.nx, args.ny, ppc=(args.ppc, args.ppc),
+                            precision=prec, energy_every=1,
+                            tile=(args.tile, args.tile), sim_index=rank)
+    stream = torch.cuda.Stream()
+    sim = Z.Sim(cfg)
+    sim.set_stream(stream.cuda_stream)
+    info = sim.info()
+    n_p = int(sum(info.n_particles[:2]))
+    n_cells = args.nx * args.ny
+
+    # warm-up (untimed)
+    sim.step(args.warmup)
+    sim.sync()
+
+    # ---- device-resident timed region --------------------------------
+    sim.profile_enable(True)
+    sim.profile_read(reset=True)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    sim.sync()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    prof = sim.profile_read(reset=True)
+    sim.profile_enable(False)
+    ms_max = all_max(ms, world)
+    total_ps = all_sum(float(n_p) * args.steps, world)
+    value = total_ps / (ms_max / 1e3)
+    launches = sum(v[1] for v in prof.values())
+
+    push_ms, push_n = prof.get("push_deposit", (0.0, 0))
+    push_avg_s = push_ms / max(push_n, 1) / 1e3
+    alg = algorithmic_bytes(n_p, n_cells, rb)
+    peak, peak_kind = hbm_peak()
+    achieved = alg / push_avg_s / 1e9 if push_avg_s > 0 else 0.0
+    traffic = measured_traffic(args.precision, n_p, n_cells)
+
+    # ---- e2e through the C ABI with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        host = []
+        for s in range(2):
+            n_s = int(info.n_particles[s])
+            real = torch.float64 if prec == Z.FP64 else torch.float32
+            buf = {k: torch.empty(n_s, dtype=torch.int32, pin_memory=True)
+                   for k in ("ix", "iy")}
+            for k in ("x", "y", "ux", "uy", "uz"):
+                buf[k] = torch.empty(n_s, dtype=real, pin_memory=True)
+            pinned.append(buf)
+            host.append({k: v.numpy() for k, v in buf.items()})
+            sim.particles(s, with_w=False, with_id=False, out=host[s])
+        h2d = sum(v.nbytes for h in host for v in h.values())
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(2):
+            sim.set_particles(s, host[s])
+        sim.step(args.steps)
+        recs = sim.energy()
+        for s in range(2):
+            sim.particles(s, with_w=False, with_id=False, out=host[s])
+        t1 = time.perf_counter()
+        barrier(world)
+        d2h = h2d + 88 * len(recs)
+        e2e_s = all_max(t1 - t0, world)
+        e2e = {"value": total_ps / e2e_s, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps,
+               "what": "set_particles from pinned host arrays + steps + "
+                       "energy history + get_particles to host, timed "
+                       "on the host clock"}
+        del pinned
+
+    # ---- CPU oracle baseline (rank 0 only) ----------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        nthreads = os.cpu_count() or 1
+        v, n, secs = oracle_sample(args.cpu_sample, args.ppc, 2, nthreads)
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": nthreads,
+               "kind": "oracle",
+               "sample": "%dx%d periodic box of the same plasma (%d "
+                         "particles), 2 steps, FP64, %d threads, %.1f s" %
+                         (args.cpu_sample, args.cpu_sample, n, nthreads, secs)}
+
+    if rank == 0:
+        out = {
+            "metric": "particle-steps/s", "value": value,
+            "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == Z.FP64 else "f32",
+            "data": "synthetic", "config": workload_config(args),
+            "roofline": {"bound": "hbm", "kernel": "push_deposit",
+                         "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg,
+                         "avg_launch_ms": push_avg_s * 1e3},
+            "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

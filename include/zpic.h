@@ -1,0 +1,272 @@
+/*
+ * zpic.h -- C ABI of the GB300 2D3V electromagnetic particle-in-cell step.
+ *
+ * The method is the PIC cycle of Guidotti et al., "Particle-In-Cell
+ * Simulation using Asynchronous Tasking" (arXiv 2106.12485), Sec. 2.2:
+ *   (1) bilinear interpolation of E, B at each particle,
+ *   (2) leapfrog + relativistic Boris push,
+ *   (3) exact charge-conserving (Villasenor-Buneman) current deposition,
+ *   (4) Yee-mesh FDTD advance of E, B with the current just deposited,
+ * with the spatial decomposition of Sec. 3.2 (regions with ghost cells,
+ * particles handed to neighbours, at most one cell moved per step) done
+ * here as 2D tiles on the GPU, and the laser initialisation and moving
+ * window of Sec. 4.1 (LWFA).
+ *
+ * Units: normalised, c = 1, time in 1/w_p, length in c/w_p, E and B in
+ * m c w_p / e, momenta u = gamma v.  dB/dt = -curl E, dE/dt = curl B - J.
+ *
+ * Grid: nx*ny cells of dx = box_x/nx, dy = box_y/ny.  Staggering
+ *   Ex(i+1/2, j)  Ey(i, j+1/2)  Ez(i, j)  Bx(i, j+1/2)  By(i+1/2, j)
+ *   Bz(i+1/2, j+1/2); Jx, Jy, Jz co-located with Ex, Ey, Ez.
+ * Time centring: x, E, B at integer steps, u at half steps, J at n+1/2.
+ * y is periodic; x is periodic or open (moving window).
+ *
+ * Conventions for every entry point:
+ *  - return value: ZPIC_OK (0) or a negative ZPIC_E* code; nothing throws
+ *    across the ABI; zpic_strerror() names a code and zpic_last_error()
+ *    gives the message of the last failure on the calling thread.
+ *  - handles are owned by the library and freed by the matching destroy.
+ *  - all buffers passed in are host memory owned by the caller, unless the
+ *    argument says "device"; the library copies what it needs and keeps no
+ *    pointer to caller memory after the call returns.
+ *  - zpic_step is asynchronous on the handle's stream; getters synchronise.
+ *  - one host thread at a time per handle.
+ *  - the library needs a CUDA device; with none (or without the kernels for
+ *    it) every call that would touch the device returns ZPIC_ECUDA.  There
+ *    is no CPU fallback.
+ */
+#ifndef ZPIC_H
+#define ZPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZPIC_MAX_SPECIES 8
+#define ZPIC_VERSION 1
+
+/* status codes */
+#define ZPIC_OK 0
+#define ZPIC_EINVAL (-1)    /* bad argument, NULL handle or buffer        */
+#define ZPIC_ECFL (-2)      /* dt >= 1/sqrt(1/dx^2 + 1/dy^2)              */
+#define ZPIC_ENOMEM (-3)    /* device or host allocation failed           */
+#define ZPIC_ECUDA (-4)     /* CUDA runtime error / no usable device      */
+#define ZPIC_EOVERFLOW (-5) /* particle storage exhausted after resorting */
+#define ZPIC_ENAN (-6)      /* non-finite value detected                  */
+#define ZPIC_ETIMEOUT (-7)  /* a bounded device wait gave up              */
+#define ZPIC_ECAP (-8)      /* destination buffer too small               */
+#define ZPIC_ENOTSUP (-9)   /* option not supported by this build         */
+
+/* precision of fields and particle state */
+#define ZPIC_FP32 0
+#define ZPIC_FP64 1
+
+/* x boundary (y is always periodic) */
+#define ZPIC_BC_PERIODIC 0
+#define ZPIC_BC_OPEN 1
+
+/* field selectors */
+#define ZPIC_EX 0
+#define ZPIC_EY 1
+#define ZPIC_EZ 2
+#define ZPIC_BX 3
+#define ZPIC_BY 4
+#define ZPIC_BZ 5
+#define ZPIC_JX 6
+#define ZPIC_JY 7
+#define ZPIC_JZ 8
+
+/* density profiles of the initial load (x in box units, absolute frame) */
+#define ZPIC_PROFILE_NONE 0    /* no initial particles                   */
+#define ZPIC_PROFILE_UNIFORM 1 /* n0 everywhere                          */
+#define ZPIC_PROFILE_SLAB 2    /* n0 for x0 <= x_cell < x1, else 0        */
+#define ZPIC_PROFILE_RAMP 3    /* 0 below x0, linear to n0 over length x1,
+                                  n0 beyond                               */
+
+/* config flags */
+#define ZPIC_TRACK_IDS 1       /* keep a per-particle int32 id (parity)    */
+
+typedef struct {
+    double q_over_m;    /* charge-to-mass ratio (electrons: -1)          */
+    int ppc_x, ppc_y;   /* particles per cell at density n0              */
+    int lattice;        /* 1: offsets (k+1/2)/ppc; 0: uniform random     */
+    double u_th[3];     /* thermal spread of u per axis                  */
+    double u_fl[3];     /* drift of u                                    */
+    int profile;        /* ZPIC_PROFILE_*                                */
+    double x0, x1;      /* profile parameters (see above)                */
+    double n0;          /* density; a particle carries q = sign(q/m)*w/ppc
+                           with weight w = local density                 */
+} zpic_species;
+
+typedef struct {
+    int enabled;
+    double a0;          /* normalised vector potential                   */
+    double omega0;      /* laser frequency (units of w_p)                */
+    double w0;          /* transverse waist: exp(-(y-yc)^2/w0^2) in field */
+    double fwhm;        /* intensity FWHM along x                        */
+    double x0;          /* pulse centre in x                             */
+    double y_center;    /* pulse axis in y                               */
+} zpic_laser;
+
+typedef struct {
+    int nx, ny;                 /* cells                                  */
+    double box_x, box_y;        /* box size                               */
+    double dt;                  /* time step (CFL checked)                */
+    int precision;              /* ZPIC_FP32 or ZPIC_FP64                 */
+    int bc_x;                   /* ZPIC_BC_PERIODIC or ZPIC_BC_OPEN       */
+    int moving_window;          /* 1: window moves at c along +x (needs
+                                   bc_x = ZPIC_BC_OPEN)                   */
+    int n_species;              /* 0..ZPIC_MAX_SPECIES                    */
+    zpic_species species[ZPIC_MAX_SPECIES];
+    zpic_laser laser;
+    uint64_t seed;              /* generator seed of the initial load     */
+    int sim_index;              /* generator stream of this simulation    */
+    int energy_every;           /* record energies every k steps; 0: off  */
+    int tile_x, tile_y;         /* tile size in cells; 0: library default */
+    int flags;                  /* ZPIC_TRACK_IDS                         */
+    double capacity_slack;      /* spare tile capacity fraction; 0: 0.25  */
+} zpic_config;
+
+/* Particle arrays for get/set.  Real arrays (x .. w) hold float when
+ * precision == ZPIC_FP32, double when ZPIC_FP64 (the library converts if
+ * this differs from the simulation's precision).  Offsets x, y in [0, 1)
+ * within cell (ix, iy). */
+typedef struct {
+    int precision;
+    size_t cap;         /* capacity of each array (get)                  */
+    size_t n;           /* number of particles (set: supplied, get: out) */
+    int32_t *ix, *iy;
+    void *x, *y, *ux, *uy, *uz;
+    void *w;            /* may be NULL (get: skipped; set: weight 1)     */
+    int32_t *id;        /* may be NULL (get: skipped; set: ids 0..n-1)   */
+} zpic_particles;
+
+/* One energy record: step k means fields at step k and momenta at k-1/2
+ * (after the push of step k-1).  wE = 1/2 sum E^2 dx dy, wB likewise,
+ * kin[s] = sum m_p (gamma - 1) dx dy. */
+typedef struct {
+    int32_t step;
+    int32_t n_species;
+    double wE, wB;
+    double kin[ZPIC_MAX_SPECIES];
+} zpic_energy_rec;
+
+/* Layout and state summary of a simulation. */
+typedef struct {
+    int nx, ny, ld;             /* ld = padded row length of field arrays */
+    double dx, dy, dt;
+    int tile_x, tile_y, ntiles_x, ntiles_y;
+    int precision;
+    int32_t step;               /* completed steps                        */
+    int32_t n_shift;            /* moving-window shifts so far            */
+    int n_species;
+    int64_t n_particles[ZPIC_MAX_SPECIES];
+    int64_t capacity[ZPIC_MAX_SPECIES];
+    int32_t resorts;            /* full re-sorts done (overflow recovery)  */
+    size_t device_bytes;        /* device memory held                     */
+} zpic_info;
+
+typedef struct zpic_sim zpic_sim;
+typedef struct zpic_batch zpic_batch;
+
+/* Creates a simulation: validates cfg (ZPIC_EINVAL, ZPIC_ECFL), allocates
+ * device memory, draws the initial particles on the GPU from the counter-
+ * based SplitMix64 stream (seed, sim_index, species) and writes the laser
+ * fields (Sec. 4.1).  *out receives the handle.  cfg is copied. */
+int zpic_create(const zpic_config *cfg, zpic_sim **out);
+
+/* Frees a simulation created by zpic_create (not a batch view). */
+int zpic_destroy(zpic_sim *sim);
+
+/* Enqueues n time steps (each: push+deposit, Yee, tile migration, window)
+ * on the handle's stream and returns.  Errors of earlier steps found at
+ * the last synchronisation are returned here. */
+int zpic_step(zpic_sim *sim, int n);
+
+/* Waits for all enqueued steps; recovers from tile-capacity overflow by
+ * re-sorting with more capacity and re-running the steps that were held
+ * back.  Returns the device status. */
+int zpic_sync(zpic_sim *sim);
+
+/* Uses `stream` (a cudaStream_t) for all later work of the handle.  NULL
+ * restores the library's own stream.  The caller keeps the stream alive
+ * while the handle uses it. */
+int zpic_set_stream(zpic_sim *sim, void *stream);
+
+/* Copies the interior nx*ny values of field `which` (ZPIC_EX..ZPIC_JZ),
+ * row-major dst[j*nx + i], at the current step.  J is the current of the
+ * last step.  cap is the number of elements dst holds (ZPIC_ECAP if less
+ * than nx*ny).  _f32 narrows FP64 simulations; _f64 widens FP32 ones. */
+int zpic_get_fields_f32(zpic_sim *sim, int which, float *dst, size_t cap);
+int zpic_get_fields_f64(zpic_sim *sim, int which, double *dst, size_t cap);
+
+/* Overwrites field `which` (E or B only) with n = nx*ny values. */
+int zpic_set_fields_f64(zpic_sim *sim, int which, const double *src,
+                        size_t n);
+
+/* Number of particles of a species (synchronises). */
+int zpic_num_particles(zpic_sim *sim, int species, int64_t *n);
+
+/* Copies the particles of a species into dst (tile order).  ZPIC_ECAP if
+ * dst->cap is too small; dst->n receives the count. */
+int zpic_get_particles(zpic_sim *sim, int species, const zpic_particles *dst,
+                       size_t *n_written);
+
+/* Replaces the particles of a species with src (copied to the device and
+ * sorted into tiles there).  Particles must have 0 <= ix < nx,
+ * 0 <= iy < ny and offsets in [0, 1) (ZPIC_EINVAL otherwise). */
+int zpic_set_particles(zpic_sim *sim, int species, const zpic_particles *src);
+
+/* Copies the energy history (one record per energy_every steps).  With
+ * dst == NULL and cap == 0 only *n_written is set (size query). */
+int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
+                size_t *n_written);
+
+/* Fills *info (synchronises). */
+int zpic_get_info(zpic_sim *sim, zpic_info *info);
+
+/* Per-tile particle counts of a species, tile index ty*ntiles_x + tx, in
+ * the order zpic_get_particles writes them. */
+int zpic_get_tile_counts(zpic_sim *sim, int species, int32_t *dst,
+                         size_t cap);
+
+/* Kernel timing: when enabled, zpic_step launches kernels one by one and
+ * records a CUDA event pair around each launch on the handle's stream.
+ * zpic_profile_read returns, per kernel name, the summed device time (ms)
+ * and the number of launches since the last reset (synchronises). */
+int zpic_profile_enable(zpic_sim *sim, int enable);
+int zpic_profile_read(zpic_sim *sim, char *names, size_t name_len,
+                      double *ms_total, int32_t *launches, int cap, int *n,
+                      int reset);
+
+/* Batched simulations (independent; same precision): one launch per stage
+ * advances all of them over a (simulation, tile) work list, captured in a
+ * CUDA graph.  zpic_batch_sim gives a view handle for the getters; views
+ * are freed with the batch. */
+int zpic_batch_create(const zpic_config *cfgs, int n, zpic_batch **out);
+int zpic_batch_step(zpic_batch *b, int n);
+int zpic_batch_sync(zpic_batch *b);
+int zpic_batch_sim(zpic_batch *b, int i, zpic_sim **view);
+int zpic_batch_set_stream(zpic_batch *b, void *stream);
+int zpic_batch_profile_enable(zpic_batch *b, int enable);
+int zpic_batch_destroy(zpic_batch *b);
+
+/* Allocation hooks for the device memory of handles created afterwards
+ * (NULL, NULL restores cudaMalloc/cudaFree).  alloc returns a device
+ * pointer aligned to 256 bytes or NULL; both get the handle's stream. */
+typedef void *(*zpic_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*zpic_free_fn)(void *ptr, size_t bytes, void *stream,
+                             void *ctx);
+int zpic_set_allocator(zpic_alloc_fn alloc, zpic_free_fn free_fn, void *ctx);
+
+const char *zpic_strerror(int code);
+const char *zpic_last_error(void);
+int zpic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZPIC_H */

@@ -1,0 +1,295 @@
+// k_field.cu -- field kernels: fused Yee step (PIC stage 4 of Sec. 2.2),
+// laser initialisation (Sec. 4.1), and the end-of-step bookkeeping
+// (energy records, moving-window counter, step counter).
+//
+// Yee step, one CTA per 32 x 8 block of cells, temporal blocking of the three
+// sub-steps inside the block:
+//   load E^n on [-1, 33] x [-1, 9], B^n on [-1, 32] x [-1, 8], J on [0, 32]^2
+//   B^{n+1/2} = B^n - (dt/2) curl E^n        on [-1, 32] x [-1, 8]
+//   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J) on [0, 32] x [0, 8]
+//   B^{n+1}   = B^{n+1/2} - (dt/2) curl E^{n+1} on the block's own cells
+// and writes E^{n+1}, B^{n+1} of its own cells to the other field copy, one
+// cell to the left when the moving window shifts this step.  HBM traffic per
+// cell: read E, B, J (9 values), write E, B (6) and zero the other J (3).
+#include <math.h>
+
+#include "zpic_dev.cuh"
+#include "zpic_kernels.h"
+
+namespace zp {
+
+// periodic index for any i (the 34 x 10 halo can exceed twice a tiny grid)
+__device__ __forceinline__ int wrapg(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+template <typename R>
+__device__ __forceinline__ R fld(const SimDev<R> &S, const R *f, int gi,
+                                 int gj) {
+  gj = wrapg(gj, S.ny);
+  if (S.open_x) {
+    if (gi < 0 || gi >= S.nx) return R(0);
+  } else {
+    gi = wrapg(gi, S.nx);
+  }
+  return f[(size_t)gj * S.ld + gi];
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;  // valid in warp 0 lane 0 (and every warp's lane 0)
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    yee_kernel(const SimDev<R> *__restrict__ sims,
+               const int2 *__restrict__ items, BatchStatus *st) {
+  constexpr int X = kYeeX, Y = kYeeY;
+  constexpr int EW = X + 3, EH = Y + 3;   // E^n on [-1, X+1]
+  constexpr int BW = X + 2, BH = Y + 2;   // B on [-1, X]
+  constexpr int JW = X + 1, JH = Y + 1;   // J on [0, X]
+  __shared__ R se[3][EH][EW];
+  __shared__ R sb[3][BH][BW];
+  __shared__ R sj[3][JH][JW];
+  __shared__ double red[kWarps];
+
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const int2 it = items[blockIdx.x];
+  const SimDev<R> &S = sims[it.x];
+  const int bx = it.y % S.ybx, by = it.y / S.ybx;
+  const int x0 = bx * X, y0 = by * Y;
+  const int cur = step & 1, nxt = cur ^ 1;
+  const int shift = shift_due(S, step, S.moving_window ? *S.n_shift : 0);
+  const bool do_energy =
+      S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
+  const R dt = S.dt, h = R(0.5) * S.dt;
+  const R rdx = R(1) / S.dx, rdy = R(1) / S.dy;
+
+  for (int k = threadIdx.x; k < 3 * EH * EW; k += blockDim.x) {
+    const int c = k / (EH * EW), r = k - c * (EH * EW);
+    const int lj = r / EW, li = r - lj * EW;
+    se[c][lj][li] = fld(S, S.E[cur][c], x0 - 1 + li, y0 - 1 + lj);
+  }
+  for (int k = threadIdx.x; k < 3 * BH * BW; k += blockDim.x) {
+    const int c = k / (BH * BW), r = k - c * (BH * BW);
+    const int lj = r / BW, li = r - lj * BW;
+    sb[c][lj][li] = fld(S, S.B[cur][c], x0 - 1 + li, y0 - 1 + lj);
+  }
+  for (int k = threadIdx.x; k < 3 * JH * JW; k += blockDim.x) {
+    const int c = k / (JH * JW), r = k - c * (JH * JW);
+    const int lj = r / JW, li = r - lj * JW;
+    sj[c][lj][li] = fld(S, S.J[cur][c], x0 + li, y0 + lj);
+  }
+  __syncthreads();
+
+  // B^{n+1/2} on local [-1, X] x [-1, Y]; sb index = local + 1
+  for (int k = threadIdx.x; k < BH * BW; k += blockDim.x) {
+    const int lj = k / BW, li = k - lj * BW;  // local (li-1, lj-1)
+    // E(i, j) is se[.][lj][li]; E(i+1, j) se[.][lj][li+1]; E(i, j+1) se[.][lj+1][li]
+    const R ez = se[2][lj][li];
+    const R nbx = sb[0][lj][li] - h * (se[2][lj + 1][li] - ez) * rdy;
+    const R nby = sb[1][lj][li] + h * (se[2][lj][li + 1] - ez) * rdx;
+    const R nbz = sb[2][lj][li] - h * ((se[1][lj][li + 1] - se[1][lj][li]) * rdx -
+                                       (se[0][lj + 1][li] - se[0][lj][li]) * rdy);
+    const int gi = x0 - 1 + li;
+    const bool out = S.open_x && (gi < 0 || gi >= S.nx);
+    sb[0][lj][li] = out ? R(0) : nbx;
+    sb[1][lj][li] = out ? R(0) : nby;
+    sb[2][lj][li] = out ? R(0) : nbz;
+  }
+  __syncthreads();
+
+  // E^{n+1} on local [0, X] x [0, Y]: se index = local + 1, sb index = local + 1
+  for (int k = threadIdx.x; k < JH * JW; k += blockDim.x) {
+    const int j = k / JW, i = k - j * JW;
+    const R bzc = sb[2][j + 1][i + 1];
+    const R nex = se[0][j + 1][i + 1] +
+                  dt * ((bzc - sb[2][j][i + 1]) * rdy - sj[0][j][i]);
+    const R ney = se[1][j + 1][i + 1] +
+                  dt * (-(bzc - sb[2][j + 1][i]) * rdx - sj[1][j][i]);
+    const R nez = se[2][j + 1][i + 1] +
+                  dt * ((sb[1][j + 1][i + 1] - sb[1][j + 1][i]) * rdx -
+                        (sb[0][j + 1][i + 1] - sb[0][j][i + 1]) * rdy -
+                        sj[2][j][i]);
+    const int gi = x0 + i;
+    const bool out = S.open_x && gi >= S.nx;
+    se[0][j + 1][i + 1] = out ? R(0) : nex;
+    se[1][j + 1][i + 1] = out ? R(0) : ney;
+    se[2][j + 1][i + 1] = out ? R(0) : nez;
+  }
+  __syncthreads();
+
+  // B^{n+1} on the block's own cells (one per thread) and write back
+  const int i = threadIdx.x % X, j = threadIdx.x / X;
+  const int gi = x0 + i, gj = y0 + j;
+  double e2 = 0.0, b2 = 0.0;
+  if (gi < S.nx && gj < S.ny) {
+    const R ez = se[2][j + 1][i + 1];
+    const R nbx = sb[0][j + 1][i + 1] - h * (se[2][j + 2][i + 1] - ez) * rdy;
+    const R nby = sb[1][j + 1][i + 1] + h * (se[2][j + 1][i + 2] - ez) * rdx;
+    const R nbz = sb[2][j + 1][i + 1] -
+                  h * ((se[1][j + 1][i + 2] - se[1][j + 1][i + 1]) * rdx -
+                       (se[0][j + 2][i + 1] - se[0][j + 1][i + 1]) * rdy);
+    const R ex = se[0][j + 1][i + 1], ey = se[1][j + 1][i + 1];
+    if (do_energy) {
+      e2 = (double)(ex * ex + ey * ey + ez * ez);
+      b2 = (double)(nbx * nbx + nby * nby + nbz * nbz);
+    }
+    const size_t row = (size_t)gj * S.ld;
+    const int wi = gi - shift;
+    if (wi >= 0) {
+      S.E[nxt][0][row + wi] = ex;
+      S.E[nxt][1][row + wi] = ey;
+      S.E[nxt][2][row + wi] = ez;
+      S.B[nxt][0][row + wi] = nbx;
+      S.B[nxt][1][row + wi] = nby;
+      S.B[nxt][2][row + wi] = nbz;
+    }
+    if (shift && gi == S.nx - 1) {  // the column entering the window
+      for (int c = 0; c < 3; ++c) {
+        S.E[nxt][c][row + gi] = R(0);
+        S.B[nxt][c][row + gi] = R(0);
+      }
+    }
+    for (int c = 0; c < 3; ++c) S.J[nxt][c][row + gi] = R(0);
+  }
+  if (do_energy) {
+    const size_t b = (size_t)it.y * 2;
+    e2 = block_sum(e2, red);
+    if (threadIdx.x == 0) S.part_fld[b] = e2;
+    b2 = block_sum(b2, red);
+    if (threadIdx.x == 0) S.part_fld[b + 1] = b2;
+  }
+}
+
+template <typename R>
+cudaError_t launch_yee(const SimDev<R> *sims, const int2 *items, int n_items,
+                       BatchStatus *st, cudaStream_t stream) {
+  if (n_items == 0) return cudaSuccess;
+  yee_kernel<R><<<n_items, kThreads, 0, stream>>>(sims, items, st);
+  return cudaGetLastError();
+}
+
+// ---- end of step ----------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    end_step_kernel(const SimDev<R> *__restrict__ sims, BatchStatus *st) {
+  __shared__ double red[kWarps];
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const SimDev<R> &S = sims[blockIdx.x];
+  const bool do_energy =
+      S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
+  if (do_energy) {
+    const int ntiles = S.ntx * S.nty;
+    double kin[kMaxSpecies];
+    for (int s = 0; s < S.nsp; ++s) {
+      double v = 0.0;
+      for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        v += S.part_kin[(size_t)t * kMaxSpecies + s];
+      kin[s] = block_sum(v, red) * S.sp[s].kin_scale;
+    }
+    const int nyb = S.ybx * S.yby;
+    double e = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nyb; t += blockDim.x) {
+      e += S.part_fld[2 * (size_t)t];
+      b += S.part_fld[2 * (size_t)t + 1];
+    }
+    e = block_sum(e, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) {
+      const int rec = (step + 1) / S.energy_every - 1;
+      const double area = S.dx_d * S.dy_d;
+      bool bad = !isfinite(e) || !isfinite(b);
+      if (rec < S.hist_cap) {
+        zpic_energy_rec &r = S.hist[rec];
+        r.step = step + 1;
+        r.n_species = S.nsp;
+        r.wE = 0.5 * e * area;
+        r.wB = 0.5 * b * area;
+        for (int s = 0; s < kMaxSpecies; ++s) {
+          r.kin[s] = s < S.nsp ? kin[s] : 0.0;
+          if (s < S.nsp && !isfinite(kin[s])) bad = true;
+        }
+        *S.hist_n = rec + 1;
+      }
+      if (bad) {
+        atomicOr(&st->error, ERR_NAN);
+        atomicMin(&st->err_step, step);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (S.moving_window && shift_due(S, step, *S.n_shift)) *S.n_shift += 1;
+    __threadfence();
+    const int t = atomicAdd(&st->blocks_done, 1);
+    if (t == (int)gridDim.x - 1) {
+      st->blocks_done = 0;
+      __threadfence();
+      st->step = step + 1;
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
+                            BatchStatus *st, cudaStream_t stream) {
+  end_step_kernel<R><<<n_sims, kThreads, 0, stream>>>(sims, st);
+  return cudaGetLastError();
+}
+
+// ---- laser initialisation ------------------------------------------------
+
+// Gaussian pulse, linear polarisation along y, propagating in +x:
+// Ey = E0 exp(-(y-yc)^2/w0^2) exp(-2 ln2 (x-x0)^2/fwhm^2) cos(omega0 (x-x0))
+// at the Ey points, and Bz = Ey (a +x wave) at the Bz points.
+__device__ __forceinline__ double laser_value(const LaserParams &lp, double X,
+                                              double Y) {
+  const double dX = X - lp.x0, dY = Y - lp.yc;
+  return lp.E0 * exp(-dY * dY / (lp.w0 * lp.w0)) *
+         exp(-2.0 * log(2.0) * dX * dX / (lp.fwhm * lp.fwhm)) *
+         cos(lp.omega0 * dX);
+}
+
+template <typename R>
+__global__ void laser_kernel(const SimDev<R> *__restrict__ sim,
+                             LaserParams lp) {
+  const SimDev<R> &S = *sim;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= S.nx || j >= S.ny) return;
+  const double dx = S.dx_d, dy = S.dy_d;
+  const size_t k = (size_t)j * S.ld + i;
+  S.E[0][1][k] += (R)laser_value(lp, i * dx, (j + 0.5) * dy);
+  S.B[0][2][k] += (R)laser_value(lp, (i + 0.5) * dx, (j + 0.5) * dy);
+}
+
+template <typename R>
+cudaError_t launch_laser(const SimDev<R> *sim_dev, int nx, int ny,
+                         LaserParams lp, cudaStream_t stream) {
+  dim3 grid((nx + 127) / 128, ny);
+  laser_kernel<R><<<grid, 128, 0, stream>>>(sim_dev, lp);
+  return cudaGetLastError();
+}
+
+#define ZP_INST(R)                                                          \
+  template cudaError_t launch_yee<R>(const SimDev<R> *, const int2 *, int, \
+                                     BatchStatus *, cudaStream_t);          \
+  template cudaError_t launch_end_step<R>(const SimDev<R> *, int,          \
+                                          BatchStatus *, cudaStream_t);     \
+  template cudaError_t launch_laser<R>(const SimDev<R> *, int, int,        \
+                                       LaserParams, cudaStream_t);
+ZP_INST(float)
+ZP_INST(double)
+#undef ZP_INST
+
+}  // namespace zp

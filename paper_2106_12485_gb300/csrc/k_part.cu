@@ -1,0 +1,437 @@
+// k_part.cu -- particle store management: tile migration (the particle
+// hand-over between neighbouring regions of Sec. 3.2, at most one cell per
+// step so only the 8 neighbour tiles can receive), moving-window injection
+// (Sec. 4.1), the initial load, and binning / compaction used by set/get and
+// by the overflow re-sort.
+#include <math.h>
+
+#include "zpic_dev.cuh"
+#include "zpic_kernels.h"
+
+namespace zp {
+
+// ---- migration --------------------------------------------------------------
+//
+// One CTA per tile: scans the outboxes of its distinct neighbour tiles, keeps
+// the entries whose cell lies in this tile and appends them behind the tile's
+// stayers (warp-aggregated slot claims on a shared cursor).  Tiles in the last
+// column also receive the new plasma column when the window shifts.  Particles
+// that find no room go to the overflow buffer and raise ERR_OVERFLOW.
+
+template <typename R>
+__device__ __forceinline__ void park(OverflowDev<R> &ovf, BatchStatus *st,
+                                     int step, int sim, int s, int ix, int iy,
+                                     int id, R x, R y, R ux, R uy, R uz, R w) {
+  const int o = atomicAdd(&st->ovf_count, 1);
+  if (o < ovf.cap) {
+    ovf.sim[o] = sim;
+    ovf.species[o] = s;
+    ovf.ix[o] = ix;
+    ovf.iy[o] = iy;
+    ovf.id[o] = id;
+    ovf.x[o] = x;
+    ovf.y[o] = y;
+    ovf.ux[o] = ux;
+    ovf.uy[o] = uy;
+    ovf.uz[o] = uz;
+    ovf.w[o] = w;
+    atomicOr(&st->error, ERR_OVERFLOW);
+  } else {
+    atomicAdd(&st->lost, 1);
+    atomicOr(&st->error, ERR_LOST);
+  }
+  atomicMin(&st->err_step, step);
+}
+
+template <typename R>
+__device__ __forceinline__ double window_density(const SpeciesDev<R> &P,
+                                                 double xa) {
+  if (xa < P.ramp_x0) return 0.0;
+  if (P.ramp_len > 0.0 && xa < P.ramp_x0 + P.ramp_len)
+    return P.n0 * (xa - P.ramp_x0) / P.ramp_len;
+  return P.n0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    migrate_kernel(const SimDev<R> *__restrict__ sims,
+                   const int2 *__restrict__ items, BatchStatus *st,
+                   OverflowDev<R> ovf) {
+  __shared__ int nbl[8];
+  __shared__ int nnb;
+  __shared__ int cursor;
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const int2 it = items[blockIdx.x];
+  const SimDev<R> &S = sims[it.x];
+  const int tile = it.y;
+  const int tcx = tile % S.ntx, tcy = tile / S.ntx;
+  const int x0 = tcx * S.tx, y0 = tcy * S.ty;
+  const int tw = min(S.tx, S.nx - x0), th = min(S.ty, S.ny - y0);
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy) continue;
+        int cx = tcx + dx;
+        const int cy = wrap1(tcy + dy, S.nty);
+        if (S.open_x) {
+          if (cx < 0 || cx >= S.ntx) continue;
+        } else {
+          cx = wrap1(cx, S.ntx);
+        }
+        const int nb = cy * S.ntx + cx;
+        bool dup = nb == tile;
+        for (int q = 0; q < m; ++q) dup |= nbl[q] == nb;
+        if (!dup) nbl[m++] = nb;
+      }
+    nnb = m;
+  }
+  const int nsh = S.moving_window ? *S.n_shift : 0;
+  const bool shift = shift_due(S, step, nsh);
+  const bool inject_col = shift && (x0 + tw == S.nx);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+
+  for (int s = 0; s < S.nsp; ++s) {
+    const SpeciesDev<R> &P = S.sp[s];
+    __syncthreads();
+    if (threadIdx.x == 0) cursor = 0;
+    __syncthreads();
+    const int n_stay = P.cnt[tile];
+    const int cap = P.cap[tile];
+    const size_t base = (size_t)P.off[tile];
+    for (int q = 0; q < nnb; ++q) {
+      const int nb = nbl[q];
+      const int m = P.ob_cnt[nb];
+      const size_t ob = (size_t)nb * P.ob_cap;
+      for (int k0 = 0; k0 < m; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        bool mine = false;
+        int ix = 0, iy = 0;
+        if (k < m) {
+          ix = P.ob_ix[ob + k];
+          iy = P.ob_iy[ob + k];
+          mine = (iy / S.ty) * S.ntx + ix / S.tx == tile;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        if (!bal) continue;
+        const int leader = __ffs(bal) - 1;
+        int wb = 0;
+        if (lane == leader) wb = atomicAdd(&cursor, __popc(bal));
+        wb = __shfl_sync(0xffffffffu, wb, leader);
+        if (!mine) continue;
+        const size_t e = ob + k;
+        const int d = n_stay + wb + __popc(bal & lt);
+        const R w = P.w ? P.ob_w[e] : R(1);
+        const int id = P.id ? P.ob_id[e] : 0;
+        if (d < cap) {
+          const size_t t = base + d;
+          P.ix[t] = ix;
+          P.iy[t] = iy;
+          P.x[t] = P.ob_x[e];
+          P.y[t] = P.ob_y[e];
+          P.ux[t] = P.ob_ux[e];
+          P.uy[t] = P.ob_uy[e];
+          P.uz[t] = P.ob_uz[e];
+          if (P.w) P.w[t] = w;
+          if (P.id) P.id[t] = id;
+        } else {
+          park(ovf, st, step, it.x, s, ix, iy, id, P.ob_x[e], P.ob_y[e],
+               P.ob_ux[e], P.ob_uy[e], P.ob_uz[e], w);
+        }
+      }
+    }
+    // moving window: cold plasma on a lattice enters through column nx-1
+    if (inject_col && P.inj_ppc_x > 0) {
+      const int ppx = P.inj_ppc_x, ppc = ppx * P.inj_ppc_y;
+      const int i = S.nx - 1;
+      const double xa = (i + nsh + 1 + 0.5) * S.dx_d;  // lab frame
+      const double dens = window_density(P, xa);
+      if (dens > 0.0) {
+        const int total = th * ppc;
+        for (int k0 = 0; k0 < total; k0 += blockDim.x) {
+          const int k = k0 + threadIdx.x;
+          const bool mine = k < total;
+          const unsigned bal = __ballot_sync(0xffffffffu, mine);
+          const int leader = __ffs(bal) - 1;
+          int wb = 0;
+          if (lane == leader) wb = atomicAdd(&cursor, __popc(bal));
+          wb = __shfl_sync(0xffffffffu, wb, leader);
+          if (!mine) continue;
+          const int j = y0 + k / ppc, kk = k % ppc;
+          const int kx = kk % ppx, ky = kk / ppx;
+          const R x = (R)((kx + 0.5) / ppx), y = (R)((ky + 0.5) / P.inj_ppc_y);
+          const int id =
+              (int)(P.id_base + ((long long)nsh * S.ny + j) * ppc + kk);
+          const int d = n_stay + wb + __popc(bal & lt);
+          if (d < cap) {
+            const size_t t = base + d;
+            P.ix[t] = i;
+            P.iy[t] = j;
+            P.x[t] = x;
+            P.y[t] = y;
+            P.ux[t] = R(0);
+            P.uy[t] = R(0);
+            P.uz[t] = R(0);
+            if (P.w) P.w[t] = (R)dens;
+            if (P.id) P.id[t] = id;
+          } else {
+            park(ovf, st, step, it.x, s, i, j, id, x, y, R(0), R(0), R(0),
+                 (R)dens);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) P.cnt[tile] = min(n_stay + cursor, cap);
+  }
+}
+
+template <typename R>
+cudaError_t launch_migrate(const SimDev<R> *sims, const int2 *items,
+                           int n_items, BatchStatus *st,
+                           const OverflowDev<R> &ovf, cudaStream_t stream) {
+  if (n_items == 0) return cudaSuccess;
+  migrate_kernel<R><<<n_items, kThreads, 0, stream>>>(sims, items, st, ovf);
+  return cudaGetLastError();
+}
+
+// ---- initial load -------------------------------------------------------
+//
+// One CTA per tile.  The tile's loaded cells are the columns
+// [max(x0, col_lo), min(x0+tw, col_hi)) x all its rows; its segment holds
+// ppc particles per loaded cell in k-major order (particle q -> k = q / nc,
+// local cell q % nc) so neighbouring particles sit in different cells.
+// Draw d of particle (cell c, k) is output (c*ppc + k)*8 + d + 1 of the
+// SplitMix64 stream `key`: d = 0, 1 offsets, 2..5 Box-Muller normals.
+
+__device__ __forceinline__ double unit53(uint64_t z) {
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    init_load_kernel(const SimDev<R> *__restrict__ sim, LoadParams lp) {
+  const SimDev<R> &S = *sim;
+  const SpeciesDev<R> &P = S.sp[lp.species];
+  const int tile = blockIdx.x;
+  const int tcx = tile % S.ntx, tcy = tile / S.ntx;
+  const int x0 = tcx * S.tx, y0 = tcy * S.ty;
+  const int tw = min(S.tx, S.nx - x0), th = min(S.ty, S.ny - y0);
+  const int ca = max(x0, lp.col_lo), cb = min(x0 + tw, lp.col_hi);
+  if (cb <= ca) return;
+  const int nca = cb - ca, nc = nca * th;
+  const int ppc = lp.ppc_x * lp.ppc_y;
+  const size_t base = (size_t)P.off[tile];
+  const bool thermal = lp.u_th[0] != 0.0 || lp.u_th[1] != 0.0 || lp.u_th[2] != 0.0;
+  const int total = nc * ppc;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    const int k = q / nc, lc = q - k * nc;
+    const int ix = ca + lc % nca, iy = y0 + lc / nca;
+    const long long c = (long long)iy * S.nx + ix;
+    const uint64_t ctr = ((uint64_t)c * ppc + k) * 8ull;
+    double x, y;
+    if (lp.lattice) {
+      x = (k % lp.ppc_x + 0.5) / lp.ppc_x;
+      y = (k / lp.ppc_x + 0.5) / lp.ppc_y;
+    } else {
+      x = (double)(sm_out(lp.key, ctr + 1) >> 40) * 0x1.0p-24;
+      y = (double)(sm_out(lp.key, ctr + 2) >> 40) * 0x1.0p-24;
+    }
+    double u[3] = {lp.u_fl[0], lp.u_fl[1], lp.u_fl[2]};
+    if (thermal) {
+      double nrm[3];
+      for (int pr = 0; pr < 2; ++pr) {
+        const double u1 =
+            ((double)(sm_out(lp.key, ctr + 3 + 2 * pr) >> 11) + 1.0) * 0x1.0p-53;
+        const double u2 = unit53(sm_out(lp.key, ctr + 4 + 2 * pr));
+        const double r = sqrt(-2.0 * log(u1));
+        const double a = 2.0 * M_PI * u2;
+        nrm[2 * pr] = r * cos(a);
+        if (pr == 0) nrm[1] = r * sin(a);
+      }
+      for (int a = 0; a < 3; ++a) u[a] += lp.u_th[a] * nrm[a];
+    }
+    double w = lp.n0;
+    if (lp.profile == ZPIC_PROFILE_RAMP) {
+      const double xc = (ix + 0.5) * S.dx_d;
+      w = xc < lp.x0 + lp.x1 ? lp.n0 * (xc - lp.x0) / lp.x1 : lp.n0;
+    }
+    const size_t t = base + q;
+    P.ix[t] = ix;
+    P.iy[t] = iy;
+    P.x[t] = (R)x;
+    P.y[t] = (R)y;
+    P.ux[t] = (R)u[0];
+    P.uy[t] = (R)u[1];
+    P.uz[t] = (R)u[2];
+    if (P.w) P.w[t] = (R)w;
+    if (P.id) P.id[t] = (int)(c * ppc + k);
+  }
+}
+
+template <typename R>
+cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
+                             LoadParams lp, cudaStream_t stream) {
+  if (ntiles == 0) return cudaSuccess;
+  init_load_kernel<R><<<ntiles, kThreads, 0, stream>>>(sim_dev, lp);
+  return cudaGetLastError();
+}
+
+// ---- binning ---------------------------------------------------------------
+
+template <typename R>
+__global__ void bin_count_kernel(Staging<R> in, long long n, int nx, int ny,
+                                 int tx, int ty, int ntx, int *counts,
+                                 int *bad) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int ix = in.ix[p], iy = in.iy[p];
+    const R x = in.x[p], y = in.y[p];
+    const bool ok = ix >= 0 && ix < nx && iy >= 0 && iy < ny && x >= R(0) &&
+                    x < R(1) && y >= R(0) && y < R(1);
+    if (!ok) {
+      atomicAdd(bad, 1);
+      in.tile[p] = -1;
+      continue;
+    }
+    const int t = (iy / ty) * ntx + ix / tx;
+    in.tile[p] = t;
+    atomicAdd(&counts[t], 1);
+  }
+}
+
+template <typename R>
+cudaError_t launch_bin_count(Staging<R> in, long long n, int nx, int ny,
+                             int tx, int ty, int ntx, int *counts, int *bad,
+                             cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)((n + kThreads - 1) / kThreads < 152 * 16
+                             ? (n + kThreads - 1) / kThreads
+                             : 152 * 16);
+  bin_count_kernel<R><<<grid, kThreads, 0, stream>>>(in, n, nx, ny, tx, ty,
+                                                     ntx, counts, bad);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void bin_scatter_kernel(Staging<R> in, long long n, SpeciesDev<R> P,
+                                   int has_w, int has_id) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int t = in.tile[p];
+    if (t < 0) continue;
+    const int slot = atomicAdd(&P.cnt[t], 1);
+    const size_t d = (size_t)P.off[t] + slot;
+    P.ix[d] = in.ix[p];
+    P.iy[d] = in.iy[p];
+    P.x[d] = in.x[p];
+    P.y[d] = in.y[p];
+    P.ux[d] = in.ux[p];
+    P.uy[d] = in.uy[p];
+    P.uz[d] = in.uz[p];
+    if (P.w) P.w[d] = has_w ? in.w[p] : R(1);
+    if (P.id) P.id[d] = has_id ? in.id[p] : (int)p;
+  }
+}
+
+template <typename R>
+cudaError_t launch_bin_scatter(Staging<R> in, long long n, SpeciesDev<R> sp,
+                               int has_w, int has_id, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)((n + kThreads - 1) / kThreads < 152 * 16
+                             ? (n + kThreads - 1) / kThreads
+                             : 152 * 16);
+  bin_scatter_kernel<R><<<grid, kThreads, 0, stream>>>(in, n, sp, has_w,
+                                                       has_id);
+  return cudaGetLastError();
+}
+
+// ---- compaction to a contiguous copy ---------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    compact_kernel(SpeciesDev<R> P, const long long *dst_off, Staging<R> out) {
+  const int t = blockIdx.x;
+  const int n = P.cnt[t];
+  const size_t src = (size_t)P.off[t];
+  const size_t dst = (size_t)dst_off[t];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    out.ix[dst + k] = P.ix[src + k];
+    out.iy[dst + k] = P.iy[src + k];
+    out.x[dst + k] = P.x[src + k];
+    out.y[dst + k] = P.y[src + k];
+    out.ux[dst + k] = P.ux[src + k];
+    out.uy[dst + k] = P.uy[src + k];
+    out.uz[dst + k] = P.uz[src + k];
+    out.w[dst + k] = P.w ? P.w[src + k] : R(1);
+    out.id[dst + k] = P.id ? P.id[src + k] : 0;
+  }
+}
+
+template <typename R>
+cudaError_t launch_compact(SpeciesDev<R> sp, int ntiles,
+                           const long long *dst_off, Staging<R> out,
+                           cudaStream_t stream) {
+  if (ntiles == 0) return cudaSuccess;
+  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, dst_off, out);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void take_overflow_kernel(OverflowDev<R> ovf, int n_entries,
+                                     int sim, int species, Staging<R> out,
+                                     long long out_base, int *n_taken) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_entries;
+       e += gridDim.x * blockDim.x) {
+    if (ovf.sim[e] != sim || ovf.species[e] != species) continue;
+    const size_t d = (size_t)(out_base + atomicAdd(n_taken, 1));
+    out.ix[d] = ovf.ix[e];
+    out.iy[d] = ovf.iy[e];
+    out.id[d] = ovf.id[e];
+    out.x[d] = ovf.x[e];
+    out.y[d] = ovf.y[e];
+    out.ux[d] = ovf.ux[e];
+    out.uy[d] = ovf.uy[e];
+    out.uz[d] = ovf.uz[e];
+    out.w[d] = ovf.w[e];
+  }
+}
+
+template <typename R>
+cudaError_t launch_take_overflow(OverflowDev<R> ovf, int n_entries, int sim,
+                                 int species, Staging<R> out,
+                                 long long out_base, int *n_taken,
+                                 cudaStream_t stream) {
+  if (n_entries <= 0) return cudaSuccess;
+  const int grid = (n_entries + kThreads - 1) / kThreads;
+  take_overflow_kernel<R><<<grid < 1024 ? grid : 1024, kThreads, 0, stream>>>(
+      ovf, n_entries, sim, species, out, out_base, n_taken);
+  return cudaGetLastError();
+}
+
+#define ZP_INST(R)                                                            \
+  template cudaError_t launch_migrate<R>(const SimDev<R> *, const int2 *,    \
+                                         int, BatchStatus *,                  \
+                                         const OverflowDev<R> &,              \
+                                         cudaStream_t);                       \
+  template cudaError_t launch_init_load<R>(const SimDev<R> *, int, LoadParams, \
+                                           cudaStream_t);                     \
+  template cudaError_t launch_bin_count<R>(Staging<R>, long long, int, int,   \
+                                           int, int, int, int *, int *,       \
+                                           cudaStream_t);                     \
+  template cudaError_t launch_bin_scatter<R>(Staging<R>, long long,           \
+                                             SpeciesDev<R>, int, int,         \
+                                             cudaStream_t);                   \
+  template cudaError_t launch_compact<R>(SpeciesDev<R>, int,                  \
+                                         const long long *, Staging<R>,       \
+                                         cudaStream_t);                       \
+  template cudaError_t launch_take_overflow<R>(OverflowDev<R>, int, int, int, \
+                                               Staging<R>, long long, int *,  \
+                                               cudaStream_t);
+ZP_INST(float)
+ZP_INST(double)
+#undef ZP_INST
+
+}  // namespace zp

@@ -1,0 +1,1393 @@
+// zpic_api.cu -- host implementation of the C ABI declared in include/zpic.h.
+//
+// A zpic_batch owns everything: per-simulation device buffers (fields, tile
+// stores, outboxes, diagnostics), the descriptor table read by the kernels,
+// the (sim, tile) work lists, the status word, the overflow buffer and one
+// CUDA graph of a whole step (push+deposit -> Yee -> migrate -> end-of-step).
+// A zpic_sim is a view of one simulation of a batch; zpic_create makes a
+// batch of one and returns its only view.
+//
+// Steps run asynchronously.  Kernels hold back every step after one that
+// raised an error; zpic_sync reads the status word, and when particles were
+// parked in the overflow buffer it re-sorts the affected stores with more
+// capacity and re-issues the steps that were held back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/zpic.h"
+#include "zpic_dev.cuh"
+#include "zpic_kernels.h"
+
+using namespace zp;
+
+// ---------------------------------------------------------------------------
+// errors, allocator
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+static int cuda_fail(cudaError_t e, const char *what) {
+  return fail(ZPIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define ZP_CU(x)                                        \
+  do {                                                  \
+    cudaError_t e_ = (x);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x);    \
+  } while (0)
+#define ZP_TRY(x)                \
+  do {                           \
+    int r_ = (x);                \
+    if (r_ != ZPIC_OK) return r_; \
+  } while (0)
+
+static zpic_alloc_fn g_alloc = nullptr;
+static zpic_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+namespace {
+
+struct DevMem {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+class Allocator {
+ public:
+  explicit Allocator(cudaStream_t s)
+      : stream_(s), alloc_(g_alloc), free_(g_free), ctx_(g_alloc_ctx) {}
+  void *get(size_t bytes, size_t *total) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (alloc_) {
+      p = alloc_(bytes, stream_, ctx_);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) *total += bytes;
+    return p;
+  }
+  void put(void *p, size_t bytes, size_t *total) {
+    if (!p) return;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (free_)
+      free_(p, bytes, stream_, ctx_);
+    else
+      cudaFree(p);
+    *total -= bytes;
+  }
+  cudaStream_t stream_;
+
+ private:
+  zpic_alloc_fn alloc_;
+  zpic_free_fn free_;
+  void *ctx_;
+};
+
+int validate(const zpic_config *c) {
+  if (!c) return fail(ZPIC_EINVAL, "config is NULL");
+  if (c->nx < 4 || c->ny < 4) return fail(ZPIC_EINVAL, "nx, ny must be >= 4");
+  if ((long long)c->nx * c->ny > (1ll << 30))
+    return fail(ZPIC_EINVAL, "grid too large");
+  if (!(c->box_x > 0) || !(c->box_y > 0) || !(c->dt > 0))
+    return fail(ZPIC_EINVAL, "box and dt must be positive");
+  if (c->precision != ZPIC_FP32 && c->precision != ZPIC_FP64)
+    return fail(ZPIC_EINVAL, "precision must be ZPIC_FP32 or ZPIC_FP64");
+  if (c->bc_x != ZPIC_BC_PERIODIC && c->bc_x != ZPIC_BC_OPEN)
+    return fail(ZPIC_EINVAL, "bc_x must be periodic or open");
+  if (c->moving_window && c->bc_x != ZPIC_BC_OPEN)
+    return fail(ZPIC_EINVAL, "moving window needs bc_x = ZPIC_BC_OPEN");
+  if (c->n_species < 0 || c->n_species > ZPIC_MAX_SPECIES)
+    return fail(ZPIC_EINVAL, "n_species out of range");
+  if (c->energy_every < 0) return fail(ZPIC_EINVAL, "energy_every < 0");
+  if (c->tile_x < 0 || c->tile_y < 0 || c->tile_x == 1 || c->tile_y == 1 ||
+      c->tile_x > 64 || c->tile_y > 64)
+    return fail(ZPIC_EINVAL, "tile sizes must be 0 or in [2, 64]");
+  if (c->capacity_slack < 0 || c->capacity_slack > 16)
+    return fail(ZPIC_EINVAL, "capacity_slack out of range");
+  const double dx = c->box_x / c->nx, dy = c->box_y / c->ny;
+  const double cfl = 1.0 / std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy));
+  if (!(c->dt < cfl)) return fail(ZPIC_ECFL, "dt violates the Courant limit");
+  for (int s = 0; s < c->n_species; ++s) {
+    const zpic_species &p = c->species[s];
+    if (!(p.q_over_m != 0) || !std::isfinite(p.q_over_m))
+      return fail(ZPIC_EINVAL, "species q_over_m must be nonzero");
+    if (p.ppc_x < 1 || p.ppc_y < 1 || p.ppc_x * p.ppc_y > 4096)
+      return fail(ZPIC_EINVAL, "species ppc out of range");
+    if (p.profile < ZPIC_PROFILE_NONE || p.profile > ZPIC_PROFILE_RAMP)
+      return fail(ZPIC_EINVAL, "unknown density profile");
+    if (p.profile != ZPIC_PROFILE_NONE && !(p.n0 > 0))
+      return fail(ZPIC_EINVAL, "density n0 must be positive");
+    if (p.profile == ZPIC_PROFILE_RAMP && !(p.x1 >= 0))
+      return fail(ZPIC_EINVAL, "ramp length must be >= 0");
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(p.u_th[a]) || !std::isfinite(p.u_fl[a]) ||
+          p.u_th[a] < 0)
+        return fail(ZPIC_EINVAL, "bad thermal or drift momentum");
+  }
+  if (c->laser.enabled) {
+    const zpic_laser &l = c->laser;
+    if (!(l.w0 > 0) || !(l.fwhm > 0) || !(l.omega0 > 0))
+      return fail(ZPIC_EINVAL, "laser w0, fwhm, omega0 must be positive");
+  }
+  return ZPIC_OK;
+}
+
+// Columns [lo, hi) with a nonzero initial density.
+void profile_columns(const zpic_species &p, int nx, double dx, int *lo,
+                     int *hi) {
+  *lo = 0;
+  *hi = 0;
+  if (p.profile == ZPIC_PROFILE_NONE) return;
+  if (p.profile == ZPIC_PROFILE_UNIFORM) {
+    *hi = nx;
+    return;
+  }
+  int a = nx, b = 0;
+  for (int i = 0; i < nx; ++i) {
+    const double xc = (i + 0.5) * dx;
+    bool on;
+    if (p.profile == ZPIC_PROFILE_SLAB)
+      on = xc >= p.x0 && xc < p.x1;
+    else  // ramp: positive density beyond x0
+      on = xc > p.x0;
+    if (on) {
+      a = std::min(a, i);
+      b = std::max(b, i + 1);
+    }
+  }
+  if (b > a) {
+    *lo = a;
+    *hi = b;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// batch implementation
+// ---------------------------------------------------------------------------
+
+struct BatchBase {
+  virtual ~BatchBase() {}
+  virtual int init(const zpic_config *cfgs, int n) = 0;
+  virtual int step(int n) = 0;
+  virtual int sync() = 0;
+  virtual int set_stream(void *s) = 0;
+  virtual int get_fields(int sim, int which, void *dst, size_t cap,
+                         int want_f64) = 0;
+  virtual int set_fields_f64(int sim, int which, const double *src,
+                             size_t n) = 0;
+  virtual int num_particles(int sim, int sp, int64_t *n) = 0;
+  virtual int get_particles(int sim, int sp, const zpic_particles *dst,
+                            size_t *nw) = 0;
+  virtual int set_particles(int sim, int sp, const zpic_particles *src) = 0;
+  virtual int energy(int sim, zpic_energy_rec *dst, size_t cap,
+                     size_t *nw) = 0;
+  virtual int info(int sim, zpic_info *out) = 0;
+  virtual int tile_counts(int sim, int sp, int32_t *dst, size_t cap) = 0;
+  virtual int profile_enable(int en) = 0;
+  virtual int profile_read(char *names, size_t name_len, double *ms,
+                           int32_t *launches, int cap, int *n, int reset) = 0;
+  int n_sims = 0;
+};
+
+struct zpic_batch {
+  std::unique_ptr<BatchBase> impl;
+  std::vector<zpic_sim *> views;
+};
+struct zpic_sim {
+  zpic_batch *b;
+  int index;
+  bool owns;
+};
+
+namespace {
+
+template <typename R>
+struct SpeciesHost {
+  zpic_species cfg{};
+  bool has_w = false, has_id = false;
+  long long total_cap = 0;
+  DevMem ix, iy, id, x, y, ux, uy, uz, w;      // store
+  DevMem off, cap, cnt, ob_cnt;                 // per tile
+  DevMem ob_ix, ob_iy, ob_id, ob_x, ob_y, ob_ux, ob_uy, ob_uz, ob_w;
+  int ob_cap = 0;
+  std::vector<int> h_cnt;                       // last counts read
+};
+
+template <typename R>
+struct SimHost {
+  zpic_config cfg{};
+  int nx, ny, ld, tx, ty, ntx, nty, ntiles, ybx, yby;
+  double dx, dy, dt;
+  DevMem fields;           // 18 planes of ny * ld
+  DevMem part_kin, part_fld, hist, small;
+  int hist_cap = 0;
+  std::vector<SpeciesHost<R>> sp;
+  SimDev<R> dev{};         // host copy of the descriptor
+};
+
+template <typename R>
+struct Timer {
+  std::string name;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  double ms = 0;
+  int launches = 0;
+};
+
+template <typename R>
+class Batch : public BatchBase {
+ public:
+  ~Batch() override { release(); }
+
+  int init(const zpic_config *cfgs, int n) override {
+    n_sims = n;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+      cudaGetLastError();
+      return fail(ZPIC_ECUDA, "no CUDA device");
+    }
+    ZP_CU(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
+    stream_ = own_stream_;
+    alloc_.reset(new Allocator(stream_));
+    sims_.resize(n);
+    for (int i = 0; i < n; ++i) ZP_TRY(init_sim(i, cfgs[i]));
+    // status and overflow buffer
+    st_mem_.p = alloc_->get(sizeof(BatchStatus), &bytes_);
+    if (!st_mem_.p) return fail(ZPIC_ENOMEM, "status");
+    st_mem_.bytes = sizeof(BatchStatus);
+    ZP_TRY(reset_status());
+    long long total = 0;
+    for (auto &s : sims_)
+      for (auto &p : s.sp) total += p.total_cap;
+    ovf_cap_ = (int)std::min<long long>(1 << 26, std::max<long long>(1 << 14, total / 64));
+    ZP_TRY(alloc_overflow());
+    ZP_CU(cudaMallocHost(&h_st_, sizeof(BatchStatus)));
+    ZP_TRY(upload_descriptors());
+    ZP_TRY(build_items());
+    // initial loads and laser fields
+    for (int i = 0; i < n; ++i) ZP_TRY(initial_state(i));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  // ---- stepping ------------------------------------------------------------
+
+  int step(int n) override {
+    if (n < 0) return fail(ZPIC_EINVAL, "negative step count");
+    if (sticky_) return sticky_;
+    target_ += n;
+    return enqueue(n);
+  }
+
+  int sync() override {
+    for (int attempt = 0; attempt < 16; ++attempt) {
+      ZP_CU(cudaStreamSynchronize(stream_));
+      ZP_TRY(read_status());
+      const BatchStatus &st = *h_st_;
+      if (st.error & ERR_LOST) {
+        sticky_ = fail(ZPIC_EOVERFLOW, "particle storage exhausted");
+        return sticky_;
+      }
+      if (st.error & ERR_STORE) {
+        sticky_ = fail(ZPIC_ECUDA, "particle store corrupted (particle outside its tile)");
+        return sticky_;
+      }
+      if (st.error & ERR_NAN) {
+        sticky_ = fail(ZPIC_ENAN, "non-finite energy");
+        return sticky_;
+      }
+      if (st.error & ERR_OVERFLOW) {
+        ZP_TRY(resort_all());
+        const long long left = target_ - st.step;
+        if (left > 0) ZP_TRY(enqueue((int)left));
+        continue;
+      }
+      return ZPIC_OK;
+    }
+    sticky_ = fail(ZPIC_EOVERFLOW, "repeated tile overflow");
+    return sticky_;
+  }
+
+  int set_stream(void *s) override {
+    ZP_CU(cudaStreamSynchronize(stream_));
+    stream_ = s ? (cudaStream_t)s : own_stream_;
+    alloc_->stream_ = stream_;
+    invalidate_graph();
+    return ZPIC_OK;
+  }
+
+  // ---- fields ---------------------------------------------------------------
+
+  int get_fields(int si, int which, void *dst, size_t cap,
+                 int want_f64) override {
+    if (!dst || which < 0 || which > 8) return fail(ZPIC_EINVAL, "bad field");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    const size_t n = (size_t)S.nx * S.ny;
+    if (cap < n) return fail(ZPIC_ECAP, "field buffer too small");
+    const int step = h_st_->step;
+    const R *src;
+    if (which < 6)
+      src = which < 3 ? S.dev.E[step & 1][which] : S.dev.B[step & 1][which - 3];
+    else
+      src = S.dev.J[(step + 1) & 1][which - 6];  // last step's current
+    const bool same = want_f64 == (sizeof(R) == 8);
+    if (same) {
+      ZP_CU(cudaMemcpy2DAsync(dst, S.nx * sizeof(R), src, S.ld * sizeof(R),
+                              S.nx * sizeof(R), S.ny, cudaMemcpyDeviceToHost,
+                              stream_));
+      ZP_CU(cudaStreamSynchronize(stream_));
+      return ZPIC_OK;
+    }
+    std::vector<R> tmp(n);
+    ZP_CU(cudaMemcpy2DAsync(tmp.data(), S.nx * sizeof(R), src, S.ld * sizeof(R),
+                            S.nx * sizeof(R), S.ny, cudaMemcpyDeviceToHost,
+                            stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    if (want_f64) {
+      double *d = (double *)dst;
+      for (size_t k = 0; k < n; ++k) d[k] = (double)tmp[k];
+    } else {
+      float *d = (float *)dst;
+      for (size_t k = 0; k < n; ++k) d[k] = (float)tmp[k];
+    }
+    return ZPIC_OK;
+  }
+
+  int set_fields_f64(int si, int which, const double *src,
+                     size_t n) override {
+    if (!src || which < 0 || which > 5) return fail(ZPIC_EINVAL, "bad field");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    if (n != (size_t)S.nx * S.ny) return fail(ZPIC_EINVAL, "size != nx*ny");
+    std::vector<R> tmp(n);
+    for (size_t k = 0; k < n; ++k) tmp[k] = (R)src[k];
+    const int step = h_st_->step;
+    R *d = which < 3 ? S.dev.E[step & 1][which] : S.dev.B[step & 1][which - 3];
+    ZP_CU(cudaMemcpy2DAsync(d, S.ld * sizeof(R), tmp.data(), S.nx * sizeof(R),
+                            S.nx * sizeof(R), S.ny, cudaMemcpyHostToDevice,
+                            stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  // ---- particles ------------------------------------------------------------
+
+  int num_particles(int si, int s, int64_t *n) override {
+    if (!n) return fail(ZPIC_EINVAL, "NULL count");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    if (s < 0 || s >= (int)S.sp.size()) return fail(ZPIC_EINVAL, "species");
+    ZP_TRY(read_counts(si, s));
+    long long t = 0;
+    for (int c : S.sp[s].h_cnt) t += c;
+    *n = t;
+    return ZPIC_OK;
+  }
+
+  int get_particles(int si, int s, const zpic_particles *d,
+                    size_t *nw) override {
+    if (!d || !d->ix || !d->iy || !d->x || !d->y || !d->ux || !d->uy || !d->uz)
+      return fail(ZPIC_EINVAL, "NULL particle array");
+    if (d->precision != ZPIC_FP32 && d->precision != ZPIC_FP64)
+      return fail(ZPIC_EINVAL, "bad precision");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    if (s < 0 || s >= (int)S.sp.size()) return fail(ZPIC_EINVAL, "species");
+    ZP_TRY(read_counts(si, s));
+    SpeciesHost<R> &P = S.sp[s];
+    std::vector<long long> off(S.ntiles);
+    long long n = 0;
+    for (int t = 0; t < S.ntiles; ++t) {
+      off[t] = n;
+      n += P.h_cnt[t];
+    }
+    if (nw) *nw = (size_t)n;
+    if ((size_t)n > d->cap) return fail(ZPIC_ECAP, "particle buffer too small");
+    ZP_TRY(ensure_staging(n + 1));
+    ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
+                          cudaMemcpyHostToDevice, stream_));
+    ZP_CU(launch_compact<R>(S.dev.sp[s], S.ntiles, (const long long *)stg_off_.p,
+                            stg_, stream_));
+    const bool same = (d->precision == ZPIC_FP64) == (sizeof(R) == 8);
+    ZP_CU(cudaMemcpyAsync(d->ix, stg_.ix, 4 * n, cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaMemcpyAsync(d->iy, stg_.iy, 4 * n, cudaMemcpyDeviceToHost, stream_));
+    if (d->id)
+      ZP_CU(cudaMemcpyAsync(d->id, stg_.id, 4 * n, cudaMemcpyDeviceToHost, stream_));
+    R *srcs[6] = {stg_.x, stg_.y, stg_.ux, stg_.uy, stg_.uz, stg_.w};
+    void *dsts[6] = {d->x, d->y, d->ux, d->uy, d->uz, d->w};
+    std::vector<R> tmp;
+    for (int a = 0; a < 6; ++a) {
+      if (!dsts[a]) continue;
+      if (same) {
+        ZP_CU(cudaMemcpyAsync(dsts[a], srcs[a], sizeof(R) * n,
+                              cudaMemcpyDeviceToHost, stream_));
+      } else {
+        tmp.resize(n);
+        ZP_CU(cudaMemcpyAsync(tmp.data(), srcs[a], sizeof(R) * n,
+                              cudaMemcpyDeviceToHost, stream_));
+        ZP_CU(cudaStreamSynchronize(stream_));
+        if (d->precision == ZPIC_FP64)
+          for (long long k = 0; k < n; ++k) ((double *)dsts[a])[k] = tmp[k];
+        else
+          for (long long k = 0; k < n; ++k) ((float *)dsts[a])[k] = (float)tmp[k];
+      }
+    }
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  int set_particles(int si, int s, const zpic_particles *src) override {
+    if (!src || (src->n > 0 && (!src->ix || !src->iy || !src->x || !src->y ||
+                                !src->ux || !src->uy || !src->uz)))
+      return fail(ZPIC_EINVAL, "NULL particle array");
+    if (src->precision != ZPIC_FP32 && src->precision != ZPIC_FP64)
+      return fail(ZPIC_EINVAL, "bad precision");
+    if (src->n > (size_t)INT_MAX) return fail(ZPIC_EINVAL, "too many particles");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    if (s < 0 || s >= (int)S.sp.size()) return fail(ZPIC_EINVAL, "species");
+    const long long n = (long long)src->n;
+    ZP_TRY(ensure_staging(n + 1));
+    const bool same = (src->precision == ZPIC_FP64) == (sizeof(R) == 8);
+    ZP_CU(cudaMemcpyAsync(stg_.ix, src->ix, 4 * n, cudaMemcpyHostToDevice, stream_));
+    ZP_CU(cudaMemcpyAsync(stg_.iy, src->iy, 4 * n, cudaMemcpyHostToDevice, stream_));
+    if (src->id)
+      ZP_CU(cudaMemcpyAsync(stg_.id, src->id, 4 * n, cudaMemcpyHostToDevice, stream_));
+    const void *srcs[6] = {src->x, src->y, src->ux, src->uy, src->uz, src->w};
+    R *dsts[6] = {stg_.x, stg_.y, stg_.ux, stg_.uy, stg_.uz, stg_.w};
+    std::vector<R> tmp;
+    for (int a = 0; a < 6; ++a) {
+      if (!srcs[a]) continue;
+      if (same) {
+        ZP_CU(cudaMemcpyAsync(dsts[a], srcs[a], sizeof(R) * n,
+                              cudaMemcpyHostToDevice, stream_));
+      } else {
+        tmp.resize(n);
+        if (src->precision == ZPIC_FP64)
+          for (long long k = 0; k < n; ++k) tmp[k] = (R)((const double *)srcs[a])[k];
+        else
+          for (long long k = 0; k < n; ++k) tmp[k] = (R)((const float *)srcs[a])[k];
+        ZP_CU(cudaMemcpyAsync(dsts[a], tmp.data(), sizeof(R) * n,
+                              cudaMemcpyHostToDevice, stream_));
+        ZP_CU(cudaStreamSynchronize(stream_));
+      }
+    }
+    if (src->w) S.sp[s].has_w = true;
+    ZP_TRY(rebuild_species(si, s, n, src->w != nullptr, src->id != nullptr,
+                           true));
+    return ZPIC_OK;
+  }
+
+  // ---- diagnostics ---------------------------------------------------------
+
+  int energy(int si, zpic_energy_rec *dst, size_t cap, size_t *nw) override {
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    int n = 0;
+    if (S.cfg.energy_every > 0)
+      ZP_CU(cudaMemcpy(&n, S.dev.hist_n, sizeof(int), cudaMemcpyDeviceToHost));
+    if (nw) *nw = (size_t)n;
+    if (n == 0 || (!dst && cap == 0)) return ZPIC_OK;  // size query
+    if (!dst) return fail(ZPIC_EINVAL, "NULL energy buffer");
+    if (cap < (size_t)n) return fail(ZPIC_ECAP, "energy buffer too small");
+    ZP_CU(cudaMemcpy(dst, S.dev.hist, sizeof(zpic_energy_rec) * n,
+                     cudaMemcpyDeviceToHost));
+    return ZPIC_OK;
+  }
+
+  int info(int si, zpic_info *o) override {
+    if (!o) return fail(ZPIC_EINVAL, "NULL info");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    std::memset(o, 0, sizeof(*o));
+    o->nx = S.nx;
+    o->ny = S.ny;
+    o->ld = S.ld;
+    o->dx = S.dx;
+    o->dy = S.dy;
+    o->dt = S.dt;
+    o->tile_x = S.tx;
+    o->tile_y = S.ty;
+    o->ntiles_x = S.ntx;
+    o->ntiles_y = S.nty;
+    o->precision = sizeof(R) == 8 ? ZPIC_FP64 : ZPIC_FP32;
+    o->step = h_st_->step;
+    int nsh = 0;
+    ZP_CU(cudaMemcpy(&nsh, S.dev.n_shift, sizeof(int), cudaMemcpyDeviceToHost));
+    o->n_shift = nsh;
+    o->n_species = (int)S.sp.size();
+    for (int s = 0; s < (int)S.sp.size(); ++s) {
+      ZP_TRY(read_counts(si, s));
+      long long t = 0;
+      for (int c : S.sp[s].h_cnt) t += c;
+      o->n_particles[s] = t;
+      o->capacity[s] = S.sp[s].total_cap;
+    }
+    o->resorts = resorts_;
+    o->device_bytes = bytes_;
+    return ZPIC_OK;
+  }
+
+  int tile_counts(int si, int s, int32_t *dst, size_t cap) override {
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    if (!dst || s < 0 || s >= (int)S.sp.size())
+      return fail(ZPIC_EINVAL, "bad argument");
+    if (cap < (size_t)S.ntiles) return fail(ZPIC_ECAP, "buffer too small");
+    ZP_TRY(read_counts(si, s));
+    std::memcpy(dst, S.sp[s].h_cnt.data(), sizeof(int) * S.ntiles);
+    return ZPIC_OK;
+  }
+
+  // ---- kernel timing --------------------------------------------------------
+
+  int profile_enable(int en) override {
+    profiling_ = en != 0;
+    return ZPIC_OK;
+  }
+
+  int profile_read(char *names, size_t name_len, double *ms, int32_t *launches,
+                   int cap, int *n, int reset) override {
+    ZP_CU(cudaStreamSynchronize(stream_));
+    int k = 0;
+    for (auto &t : timers_) {
+      for (auto &e : t.ev) {
+        float v = 0;
+        ZP_CU(cudaEventElapsedTime(&v, e.first, e.second));
+        t.ms += v;
+        t.launches += 1;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+      t.ev.clear();
+      if (k < cap) {
+        if (names && name_len > 0) {
+          std::strncpy(names + (size_t)k * name_len, t.name.c_str(), name_len - 1);
+          names[(size_t)k * name_len + name_len - 1] = 0;
+        }
+        if (ms) ms[k] = t.ms;
+        if (launches) launches[k] = t.launches;
+      }
+      ++k;
+      if (reset) {
+        t.ms = 0;
+        t.launches = 0;
+      }
+    }
+    if (n) *n = k;
+    return ZPIC_OK;
+  }
+
+ private:
+  // ---- setup ---------------------------------------------------------------
+
+  void *dalloc(DevMem &m, size_t bytes) {
+    m.p = alloc_->get(bytes, &bytes_);
+    m.bytes = m.p ? bytes : 0;
+    return m.p;
+  }
+  void dfree(DevMem &m) {
+    if (m.p) alloc_->put(m.p, m.bytes, &bytes_);
+    m.p = nullptr;
+    m.bytes = 0;
+  }
+
+  int init_sim(int i, const zpic_config &c) {
+    SimHost<R> &S = sims_[i];
+    S.cfg = c;
+    S.nx = c.nx;
+    S.ny = c.ny;
+    S.ld = (c.nx + 31) & ~31;
+    S.dx = c.box_x / c.nx;
+    S.dy = c.box_y / c.ny;
+    S.dt = c.dt;
+    S.tx = std::min(c.tile_x ? c.tile_x : 16, c.nx);
+    S.ty = std::min(c.tile_y ? c.tile_y : 16, c.ny);
+    if (push_smem_bytes<R>(S.tx, S.ty) > 200 * 1024)
+      return fail(ZPIC_EINVAL, "tile too large for shared memory");
+    S.ntx = (S.nx + S.tx - 1) / S.tx;
+    S.nty = (S.ny + S.ty - 1) / S.ty;
+    S.ntiles = S.ntx * S.nty;
+    S.ybx = (S.nx + kYeeX - 1) / kYeeX;
+    S.yby = (S.ny + kYeeY - 1) / kYeeY;
+    const size_t plane = (size_t)S.ny * S.ld;
+    if (!dalloc(S.fields, 18 * plane * sizeof(R)))
+      return fail(ZPIC_ENOMEM, "fields");
+    ZP_CU(cudaMemsetAsync(S.fields.p, 0, S.fields.bytes, stream_));
+    R *f = (R *)S.fields.p;
+    SimDev<R> &D = S.dev;
+    D.nx = S.nx;
+    D.ny = S.ny;
+    D.ld = S.ld;
+    D.tx = S.tx;
+    D.ty = S.ty;
+    D.ntx = S.ntx;
+    D.nty = S.nty;
+    D.ybx = S.ybx;
+    D.yby = S.yby;
+    D.open_x = c.bc_x == ZPIC_BC_OPEN;
+    D.moving_window = c.moving_window ? 1 : 0;
+    D.energy_every = c.energy_every;
+    D.nsp = c.n_species;
+    D.dx = (R)S.dx;
+    D.dy = (R)S.dy;
+    D.dt = (R)S.dt;
+    D.dt_dx = (R)(S.dt / S.dx);
+    D.dt_dy = (R)(S.dt / S.dy);
+    D.dx_d = S.dx;
+    D.dy_d = S.dy;
+    D.dt_d = S.dt;
+    for (int a = 0; a < 2; ++a)
+      for (int c3 = 0; c3 < 3; ++c3) {
+        D.E[a][c3] = f + (size_t)(a * 9 + c3) * plane;
+        D.B[a][c3] = f + (size_t)(a * 9 + 3 + c3) * plane;
+        D.J[a][c3] = f + (size_t)(a * 9 + 6 + c3) * plane;
+      }
+    if (!dalloc(S.part_kin, sizeof(double) * S.ntiles * kMaxSpecies) ||
+        !dalloc(S.part_fld, sizeof(double) * 2 * S.ybx * S.yby))
+      return fail(ZPIC_ENOMEM, "partials");
+    ZP_CU(cudaMemsetAsync(S.part_kin.p, 0, S.part_kin.bytes, stream_));
+    ZP_CU(cudaMemsetAsync(S.part_fld.p, 0, S.part_fld.bytes, stream_));
+    D.part_kin = (double *)S.part_kin.p;
+    D.part_fld = (double *)S.part_fld.p;
+    S.hist_cap = c.energy_every > 0 ? 4096 : 1;
+    if (!dalloc(S.hist, sizeof(zpic_energy_rec) * S.hist_cap))
+      return fail(ZPIC_ENOMEM, "history");
+    D.hist = (zpic_energy_rec *)S.hist.p;
+    D.hist_cap = S.hist_cap;
+    if (!dalloc(S.small, sizeof(int) * (2 + kMaxSpecies)))
+      return fail(ZPIC_ENOMEM, "counters");
+    ZP_CU(cudaMemsetAsync(S.small.p, 0, S.small.bytes, stream_));
+    D.hist_n = (int *)S.small.p;
+    D.n_shift = (int *)S.small.p + 1;
+    D.removed = (int *)S.small.p + 2;
+
+    // species: initial per-tile counts from the profile, then capacities
+    S.sp.resize(c.n_species);
+    const double slack = c.capacity_slack > 0 ? c.capacity_slack : 0.25;
+    for (int s = 0; s < c.n_species; ++s) {
+      SpeciesHost<R> &P = S.sp[s];
+      P.cfg = c.species[s];
+      P.has_id = (c.flags & ZPIC_TRACK_IDS) != 0;
+      // per-particle weights only where the density is not 1 everywhere
+      P.has_w = P.cfg.profile == ZPIC_PROFILE_RAMP ||
+                (P.cfg.profile != ZPIC_PROFILE_NONE && P.cfg.n0 != 1.0);
+      const int ppc = P.cfg.ppc_x * P.cfg.ppc_y;
+      int lo, hi;
+      profile_columns(P.cfg, S.nx, S.dx, &lo, &hi);
+      std::vector<int> cnt(S.ntiles, 0);
+      for (int t = 0; t < S.ntiles; ++t) {
+        const int x0 = (t % S.ntx) * S.tx, y0 = (t / S.ntx) * S.ty;
+        const int tw = std::min(S.tx, S.nx - x0), th = std::min(S.ty, S.ny - y0);
+        const int ca = std::max(x0, lo), cb = std::min(x0 + tw, hi);
+        cnt[t] = cb > ca ? (cb - ca) * th * ppc : 0;
+      }
+      const double nominal = (double)ppc * S.tx * S.ty;
+      const int min_extra = std::max(64, (int)std::ceil(nominal * slack));
+      P.ob_cap = ((std::max(64, (int)std::ceil(nominal * (c.moving_window ? 0.25 : 0.125))) + 31) / 32) * 32;
+      ZP_TRY(alloc_store(i, s, cnt, slack, min_extra));
+      // the initial load writes cnt particles per tile directly
+      ZP_CU(cudaMemcpyAsync(P.cnt.p, cnt.data(), sizeof(int) * S.ntiles,
+                            cudaMemcpyHostToDevice, stream_));
+      P.h_cnt = cnt;
+      SpeciesDev<R> &Q = D.sp[s];
+      const double qm = P.cfg.q_over_m;
+      const double q0 = (qm > 0 ? 1.0 : -1.0) / ppc;
+      Q.qm = (R)qm;
+      Q.hq = (R)(0.5 * qm * S.dt);
+      Q.q0 = (R)q0;
+      Q.qx = (R)(q0 * S.dx / S.dt);
+      Q.qy = (R)(q0 * S.dy / S.dt);
+      Q.kin_scale = q0 / qm * S.dx * S.dy;
+      Q.ob_cap = P.ob_cap;
+      if (c.moving_window && P.cfg.profile != ZPIC_PROFILE_NONE) {
+        Q.inj_ppc_x = P.cfg.ppc_x;
+        Q.inj_ppc_y = P.cfg.ppc_y;
+        // window plasma: uniform -> step at 0; ramp -> given ramp
+        Q.ramp_x0 = P.cfg.profile == ZPIC_PROFILE_RAMP ? P.cfg.x0 : -1e300;
+        Q.ramp_len = P.cfg.profile == ZPIC_PROFILE_RAMP ? P.cfg.x1 : 0.0;
+        Q.n0 = P.cfg.n0;
+        Q.id_base = (long long)S.nx * S.ny * ppc;
+      }
+    }
+    return ZPIC_OK;
+  }
+
+  // Allocates the tile store of species s for per-tile counts cnt.
+  int alloc_store(int si, int s, const std::vector<int> &cnt, double slack,
+                  int min_extra) {
+    SimHost<R> &S = sims_[si];
+    SpeciesHost<R> &P = S.sp[s];
+    std::vector<int> off(S.ntiles), cap(S.ntiles);
+    long long tot = 0;
+    for (int t = 0; t < S.ntiles; ++t) {
+      long long c = std::max<long long>((long long)std::ceil(cnt[t] * (1.0 + slack)),
+                                        (long long)cnt[t] + min_extra);
+      c = (c + 31) / 32 * 32;
+      if (tot + c > INT_MAX) return fail(ZPIC_ENOMEM, "species store exceeds 2^31");
+      off[t] = (int)tot;
+      cap[t] = (int)c;
+      tot += c;
+    }
+    // free previous store
+    for (DevMem *m : {&P.ix, &P.iy, &P.id, &P.x, &P.y, &P.ux, &P.uy, &P.uz, &P.w})
+      dfree(*m);
+    P.total_cap = tot;
+    if (!dalloc(P.ix, 4 * tot) || !dalloc(P.iy, 4 * tot) ||
+        !dalloc(P.x, sizeof(R) * tot) || !dalloc(P.y, sizeof(R) * tot) ||
+        !dalloc(P.ux, sizeof(R) * tot) || !dalloc(P.uy, sizeof(R) * tot) ||
+        !dalloc(P.uz, sizeof(R) * tot))
+      return fail(ZPIC_ENOMEM, "particle store");
+    if (P.has_w && !dalloc(P.w, sizeof(R) * tot)) return fail(ZPIC_ENOMEM, "w");
+    if (P.has_id && !dalloc(P.id, 4 * tot)) return fail(ZPIC_ENOMEM, "id");
+    if (!P.off.p) {
+      if (!dalloc(P.off, 4 * S.ntiles) || !dalloc(P.cap, 4 * S.ntiles) ||
+          !dalloc(P.cnt, 4 * S.ntiles) || !dalloc(P.ob_cnt, 4 * S.ntiles))
+        return fail(ZPIC_ENOMEM, "tile tables");
+      ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
+      const size_t nob = (size_t)P.ob_cap * S.ntiles;
+      if (!dalloc(P.ob_ix, 4 * nob) || !dalloc(P.ob_iy, 4 * nob) ||
+          !dalloc(P.ob_x, sizeof(R) * nob) || !dalloc(P.ob_y, sizeof(R) * nob) ||
+          !dalloc(P.ob_ux, sizeof(R) * nob) || !dalloc(P.ob_uy, sizeof(R) * nob) ||
+          !dalloc(P.ob_uz, sizeof(R) * nob))
+        return fail(ZPIC_ENOMEM, "outbox");
+    }
+    if (P.has_w && !P.ob_w.p &&
+        !dalloc(P.ob_w, sizeof(R) * (size_t)P.ob_cap * S.ntiles))
+      return fail(ZPIC_ENOMEM, "outbox w");
+    if (P.has_id && !P.ob_id.p &&
+        !dalloc(P.ob_id, 4 * (size_t)P.ob_cap * S.ntiles))
+      return fail(ZPIC_ENOMEM, "outbox id");
+    ZP_CU(cudaMemcpyAsync(P.off.p, off.data(), 4 * S.ntiles,
+                          cudaMemcpyHostToDevice, stream_));
+    ZP_CU(cudaMemcpyAsync(P.cap.p, cap.data(), 4 * S.ntiles,
+                          cudaMemcpyHostToDevice, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));  // host vectors go out of scope
+    SpeciesDev<R> &Q = S.dev.sp[s];
+    Q.ix = (int *)P.ix.p;
+    Q.iy = (int *)P.iy.p;
+    Q.id = (int *)P.id.p;
+    Q.x = (R *)P.x.p;
+    Q.y = (R *)P.y.p;
+    Q.ux = (R *)P.ux.p;
+    Q.uy = (R *)P.uy.p;
+    Q.uz = (R *)P.uz.p;
+    Q.w = (R *)P.w.p;
+    Q.off = (int *)P.off.p;
+    Q.cap = (int *)P.cap.p;
+    Q.cnt = (int *)P.cnt.p;
+    Q.ob_cnt = (int *)P.ob_cnt.p;
+    Q.ob_ix = (int *)P.ob_ix.p;
+    Q.ob_iy = (int *)P.ob_iy.p;
+    Q.ob_id = (int *)P.ob_id.p;
+    Q.ob_x = (R *)P.ob_x.p;
+    Q.ob_y = (R *)P.ob_y.p;
+    Q.ob_ux = (R *)P.ob_ux.p;
+    Q.ob_uy = (R *)P.ob_uy.p;
+    Q.ob_uz = (R *)P.ob_uz.p;
+    Q.ob_w = (R *)P.ob_w.p;
+    return ZPIC_OK;
+  }
+
+  int alloc_overflow() {
+    const size_t n = (size_t)ovf_cap_;
+    DevMem *ints[5] = {&ov_sim_, &ov_sp_, &ov_ix_, &ov_iy_, &ov_id_};
+    DevMem *reals[6] = {&ov_x_, &ov_y_, &ov_ux_, &ov_uy_, &ov_uz_, &ov_w_};
+    for (DevMem *m : ints)
+      if (!dalloc(*m, 4 * n)) return fail(ZPIC_ENOMEM, "overflow buffer");
+    for (DevMem *m : reals)
+      if (!dalloc(*m, sizeof(R) * n)) return fail(ZPIC_ENOMEM, "overflow buffer");
+    ovf_.cap = ovf_cap_;
+    ovf_.sim = (int *)ov_sim_.p;
+    ovf_.species = (int *)ov_sp_.p;
+    ovf_.ix = (int *)ov_ix_.p;
+    ovf_.iy = (int *)ov_iy_.p;
+    ovf_.id = (int *)ov_id_.p;
+    ovf_.x = (R *)ov_x_.p;
+    ovf_.y = (R *)ov_y_.p;
+    ovf_.ux = (R *)ov_ux_.p;
+    ovf_.uy = (R *)ov_uy_.p;
+    ovf_.uz = (R *)ov_uz_.p;
+    ovf_.w = (R *)ov_w_.p;
+    return ZPIC_OK;
+  }
+
+  int reset_status() {
+    BatchStatus b{};
+    b.err_step = INT_MAX;
+    if (h_st_) b.step = h_st_->step;
+    ZP_CU(cudaMemcpyAsync(st_mem_.p, &b, sizeof(b), cudaMemcpyHostToDevice,
+                          stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    if (h_st_) *h_st_ = b;
+    return ZPIC_OK;
+  }
+
+  int read_status() {
+    ZP_CU(cudaMemcpyAsync(h_st_, st_mem_.p, sizeof(BatchStatus),
+                          cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  int upload_descriptors() {
+    if (!sims_dev_.p && !dalloc(sims_dev_, sizeof(SimDev<R>) * n_sims))
+      return fail(ZPIC_ENOMEM, "descriptors");
+    std::vector<SimDev<R>> h(n_sims);
+    for (int i = 0; i < n_sims; ++i) h[i] = sims_[i].dev;
+    ZP_CU(cudaMemcpyAsync(sims_dev_.p, h.data(), sizeof(SimDev<R>) * n_sims,
+                          cudaMemcpyHostToDevice, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  // Work lists: particle tiles sorted by decreasing load (longest first),
+  // Yee blocks in grid order.
+  int build_items() {
+    std::vector<std::pair<long long, int2>> load;
+    int yee_n = 0;
+    max_tx_ = max_ty_ = 2;
+    for (int i = 0; i < n_sims; ++i) {
+      SimHost<R> &S = sims_[i];
+      max_tx_ = std::max(max_tx_, S.tx);
+      max_ty_ = std::max(max_ty_, S.ty);
+      for (int t = 0; t < S.ntiles; ++t) {
+        long long l = 0;
+        for (auto &P : S.sp) l += P.h_cnt.empty() ? 0 : P.h_cnt[t];
+        load.push_back({l, make_int2(i, t)});
+      }
+      yee_n += S.ybx * S.yby;
+    }
+    std::stable_sort(load.begin(), load.end(),
+                     [](const std::pair<long long, int2> &a,
+                        const std::pair<long long, int2> &b) {
+                       return a.first > b.first;
+                     });
+    std::vector<int2> items(load.size()), yee;
+    for (size_t k = 0; k < load.size(); ++k) items[k] = load[k].second;
+    yee.reserve(yee_n);
+    for (int i = 0; i < n_sims; ++i)
+      for (int b = 0; b < sims_[i].ybx * sims_[i].yby; ++b)
+        yee.push_back(make_int2(i, b));
+    if (!items_.p) {
+      if (!dalloc(items_, sizeof(int2) * std::max<size_t>(1, items.size())) ||
+          !dalloc(yee_items_, sizeof(int2) * std::max<size_t>(1, yee.size())))
+        return fail(ZPIC_ENOMEM, "work lists");
+    }
+    n_items_ = (int)items.size();
+    n_yee_ = (int)yee.size();
+    ZP_CU(cudaMemcpyAsync(items_.p, items.data(), sizeof(int2) * items.size(),
+                          cudaMemcpyHostToDevice, stream_));
+    ZP_CU(cudaMemcpyAsync(yee_items_.p, yee.data(), sizeof(int2) * yee.size(),
+                          cudaMemcpyHostToDevice, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  int initial_state(int i) {
+    SimHost<R> &S = sims_[i];
+    const SimDev<R> *dptr = (const SimDev<R> *)sims_dev_.p + i;
+    for (int s = 0; s < (int)S.sp.size(); ++s) {
+      const zpic_species &p = S.sp[s].cfg;
+      if (p.profile == ZPIC_PROFILE_NONE) continue;
+      LoadParams lp{};
+      lp.species = s;
+      lp.key = sm_out(sm_out(S.cfg.seed, (uint64_t)S.cfg.sim_index + 1),
+                      (uint64_t)s + 1);
+      lp.ppc_x = p.ppc_x;
+      lp.ppc_y = p.ppc_y;
+      lp.lattice = p.lattice;
+      for (int a = 0; a < 3; ++a) {
+        lp.u_th[a] = p.u_th[a];
+        lp.u_fl[a] = p.u_fl[a];
+      }
+      lp.profile = p.profile;
+      lp.x0 = p.x0;
+      lp.x1 = p.x1;
+      lp.n0 = p.n0;
+      profile_columns(p, S.nx, S.dx, &lp.col_lo, &lp.col_hi);
+      ZP_CU(launch_init_load<R>(dptr, S.ntiles, lp, stream_));
+    }
+    if (S.cfg.laser.enabled) {
+      const zpic_laser &l = S.cfg.laser;
+      LaserParams lp{l.a0 * l.omega0, l.omega0, l.w0, l.fwhm, l.x0, l.y_center};
+      ZP_CU(launch_laser<R>(dptr, S.nx, S.ny, lp, stream_));
+    }
+    return ZPIC_OK;
+  }
+
+  // ---- staging and re-sorting --------------------------------------------------
+
+  int ensure_staging(long long n) {
+    if (n <= stg_n_) return ZPIC_OK;
+    for (DevMem *m : {&sg_ix_, &sg_iy_, &sg_id_, &sg_tile_, &sg_x_, &sg_y_,
+                      &sg_ux_, &sg_uy_, &sg_uz_, &sg_w_})
+      dfree(*m);
+    n = std::max<long long>(n, 1024);
+    if (!dalloc(sg_ix_, 4 * n) || !dalloc(sg_iy_, 4 * n) ||
+        !dalloc(sg_id_, 4 * n) || !dalloc(sg_tile_, 4 * n) ||
+        !dalloc(sg_x_, sizeof(R) * n) || !dalloc(sg_y_, sizeof(R) * n) ||
+        !dalloc(sg_ux_, sizeof(R) * n) || !dalloc(sg_uy_, sizeof(R) * n) ||
+        !dalloc(sg_uz_, sizeof(R) * n) || !dalloc(sg_w_, sizeof(R) * n))
+      return fail(ZPIC_ENOMEM, "staging buffers");
+    stg_n_ = n;
+    stg_.ix = (int *)sg_ix_.p;
+    stg_.iy = (int *)sg_iy_.p;
+    stg_.id = (int *)sg_id_.p;
+    stg_.tile = (int *)sg_tile_.p;
+    stg_.x = (R *)sg_x_.p;
+    stg_.y = (R *)sg_y_.p;
+    stg_.ux = (R *)sg_ux_.p;
+    stg_.uy = (R *)sg_uy_.p;
+    stg_.uz = (R *)sg_uz_.p;
+    stg_.w = (R *)sg_w_.p;
+    size_t need = 0;
+    for (auto &S : sims_) need = std::max<size_t>(need, S.ntiles);
+    if (stg_off_.bytes < sizeof(long long) * (need + 1)) {
+      dfree(stg_off_);
+      if (!dalloc(stg_off_, sizeof(long long) * (need + 1)))
+        return fail(ZPIC_ENOMEM, "staging offsets");
+    }
+    if (!bad_.p && !dalloc(bad_, 4 * 2)) return fail(ZPIC_ENOMEM, "flags");
+    return ZPIC_OK;
+  }
+
+  // Re-bins n staged particles into species s of sim si (new capacities).
+  int rebuild_species(int si, int s, long long n, bool has_w, bool has_id,
+                      bool check) {
+    SimHost<R> &S = sims_[si];
+    SpeciesHost<R> &P = S.sp[s];
+    DevMem counts;
+    if (!dalloc(counts, 4 * S.ntiles)) return fail(ZPIC_ENOMEM, "counts");
+    ZP_CU(cudaMemsetAsync(counts.p, 0, 4 * S.ntiles, stream_));
+    ZP_CU(cudaMemsetAsync(bad_.p, 0, 4, stream_));
+    ZP_CU(launch_bin_count<R>(stg_, n, S.nx, S.ny, S.tx, S.ty, S.ntx,
+                              (int *)counts.p, (int *)bad_.p, stream_));
+    std::vector<int> cnt(S.ntiles);
+    int bad = 0;
+    ZP_CU(cudaMemcpyAsync(cnt.data(), counts.p, 4 * S.ntiles,
+                          cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaMemcpyAsync(&bad, bad_.p, 4, cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    dfree(counts);
+    if (bad && check)
+      return fail(ZPIC_EINVAL, "particles outside the grid or offsets not in [0,1)");
+    const double slack = S.cfg.capacity_slack > 0 ? S.cfg.capacity_slack : 0.25;
+    const double nominal = (double)P.cfg.ppc_x * P.cfg.ppc_y * S.tx * S.ty;
+    ZP_TRY(alloc_store(si, s, cnt, slack,
+                       std::max(64, (int)std::ceil(nominal * slack))));
+    ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
+    ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
+    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], has_w ? 1 : 0,
+                                has_id ? 1 : 0, stream_));
+    P.h_cnt = cnt;
+    ZP_TRY(upload_descriptors());
+    ZP_TRY(build_items());
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  int read_counts(int si, int s) {
+    SimHost<R> &S = sims_[si];
+    SpeciesHost<R> &P = S.sp[s];
+    P.h_cnt.resize(S.ntiles);
+    ZP_CU(cudaMemcpyAsync(P.h_cnt.data(), P.cnt.p, 4 * S.ntiles,
+                          cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    return ZPIC_OK;
+  }
+
+  // After ERR_OVERFLOW: every species of every sim with parked particles is
+  // compacted, joined with its overflow entries and re-binned with more room.
+  int resort_all() {
+    const int n_ovf = std::min(h_st_->ovf_count, ovf_cap_);
+    std::vector<int> osim(n_ovf), osp(n_ovf);
+    if (n_ovf > 0) {
+      ZP_CU(cudaMemcpy(osim.data(), ovf_.sim, 4 * n_ovf, cudaMemcpyDeviceToHost));
+      ZP_CU(cudaMemcpy(osp.data(), ovf_.species, 4 * n_ovf, cudaMemcpyDeviceToHost));
+    }
+    for (int si = 0; si < n_sims; ++si) {
+      SimHost<R> &S = sims_[si];
+      for (int s = 0; s < (int)S.sp.size(); ++s) {
+        int extra = 0;
+        for (int e = 0; e < n_ovf; ++e) extra += osim[e] == si && osp[e] == s;
+        if (extra == 0) continue;
+        ZP_TRY(read_counts(si, s));
+        SpeciesHost<R> &P = S.sp[s];
+        std::vector<long long> off(S.ntiles);
+        long long n = 0;
+        for (int t = 0; t < S.ntiles; ++t) {
+          off[t] = n;
+          n += P.h_cnt[t];
+        }
+        ZP_TRY(ensure_staging(n + extra + 1));
+        ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
+                              cudaMemcpyHostToDevice, stream_));
+        ZP_CU(launch_compact<R>(S.dev.sp[s], S.ntiles,
+                                (const long long *)stg_off_.p, stg_, stream_));
+        ZP_CU(cudaMemsetAsync(bad_.p, 0, 4, stream_));
+        ZP_CU(launch_take_overflow<R>(ovf_, n_ovf, si, s, stg_, n,
+                                      (int *)bad_.p, stream_));
+        ZP_CU(cudaStreamSynchronize(stream_));
+        // copies of the compacted store are in staging now; rebuild
+        ZP_TRY(rebuild_species(si, s, n + extra, S.sp[s].has_w,
+                               S.sp[s].has_id, false));
+      }
+    }
+    ++resorts_;
+    ZP_TRY(reset_status());
+    return ZPIC_OK;
+  }
+
+  // ---- launch sequence ---------------------------------------------------------
+
+  const SimDev<R> *dsims() const { return (const SimDev<R> *)sims_dev_.p; }
+  BatchStatus *dst() const { return (BatchStatus *)st_mem_.p; }
+
+  cudaError_t launch_stage(int k) {
+    switch (k) {
+      case 0:
+        return launch_push_deposit<R>(dsims(), (const int2 *)items_.p, n_items_,
+                                      max_tx_, max_ty_, dst(), ovf_, stream_);
+      case 1:
+        return launch_yee<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
+                             dst(), stream_);
+      case 2:
+        return launch_migrate<R>(dsims(), (const int2 *)items_.p, n_items_,
+                                 dst(), ovf_, stream_);
+      default:
+        return launch_end_step<R>(dsims(), n_sims, dst(), stream_);
+    }
+  }
+  static const char *stage_name(int k) {
+    static const char *names[4] = {"push_deposit", "yee", "migrate", "end_step"};
+    return names[k];
+  }
+
+  int enqueue(int n) {
+    if (n == 0) return ZPIC_OK;
+    if (profiling_) {
+      ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_));
+      if (timers_.empty())
+        for (int k = 0; k < 4; ++k) {
+          timers_.emplace_back();
+          timers_.back().name = stage_name(k);
+        }
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k) {
+          cudaEvent_t a, b;
+          ZP_CU(cudaEventCreate(&a));
+          ZP_CU(cudaEventCreate(&b));
+          ZP_CU(cudaEventRecord(a, stream_));
+          ZP_CU(launch_stage(k));
+          ZP_CU(cudaEventRecord(b, stream_));
+          timers_[k].ev.push_back({a, b});
+        }
+      return ZPIC_OK;
+    }
+    if (!graph_exec_) ZP_TRY(capture());
+    for (int i = 0; i < n; ++i) ZP_CU(cudaGraphLaunch(graph_exec_, stream_));
+    return ZPIC_OK;
+  }
+
+  int capture() {
+    // kernel attributes are set outside the capture
+    ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_));
+    cudaStream_t cs;
+    ZP_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t keep = stream_;
+    stream_ = cs;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_stage(k);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    stream_ = keep;
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&graph_exec_, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    return ZPIC_OK;
+  }
+
+  void invalidate_graph() {
+    if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
+    graph_exec_ = nullptr;
+  }
+
+  void release() {
+    if (stream_) cudaStreamSynchronize(stream_);
+    invalidate_graph();
+    for (auto &t : timers_)
+      for (auto &e : t.ev) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+    if (alloc_) {
+      for (auto &S : sims_) {
+        for (auto &P : S.sp)
+          for (DevMem *m : {&P.ix, &P.iy, &P.id, &P.x, &P.y, &P.ux, &P.uy, &P.uz,
+                            &P.w, &P.off, &P.cap, &P.cnt, &P.ob_cnt, &P.ob_ix,
+                            &P.ob_iy, &P.ob_id, &P.ob_x, &P.ob_y, &P.ob_ux,
+                            &P.ob_uy, &P.ob_uz, &P.ob_w})
+            dfree(*m);
+        for (DevMem *m : {&S.fields, &S.part_kin, &S.part_fld, &S.hist, &S.small})
+          dfree(*m);
+      }
+      for (DevMem *m : {&st_mem_, &sims_dev_, &items_, &yee_items_, &ov_sim_,
+                        &ov_sp_, &ov_ix_, &ov_iy_, &ov_id_, &ov_x_, &ov_y_,
+                        &ov_ux_, &ov_uy_, &ov_uz_, &ov_w_, &sg_ix_, &sg_iy_,
+                        &sg_id_, &sg_tile_, &sg_x_, &sg_y_, &sg_ux_, &sg_uy_,
+                        &sg_uz_, &sg_w_, &stg_off_, &bad_})
+        dfree(*m);
+    }
+    if (h_st_) cudaFreeHost(h_st_);
+    h_st_ = nullptr;
+    if (own_stream_) cudaStreamDestroy(own_stream_);
+    own_stream_ = nullptr;
+    stream_ = nullptr;
+  }
+
+  std::vector<SimHost<R>> sims_;
+  std::unique_ptr<Allocator> alloc_;
+  cudaStream_t own_stream_ = nullptr, stream_ = nullptr;
+  size_t bytes_ = 0;
+  DevMem st_mem_, sims_dev_, items_, yee_items_;
+  DevMem ov_sim_, ov_sp_, ov_ix_, ov_iy_, ov_id_, ov_x_, ov_y_, ov_ux_, ov_uy_,
+      ov_uz_, ov_w_;
+  DevMem sg_ix_, sg_iy_, sg_id_, sg_tile_, sg_x_, sg_y_, sg_ux_, sg_uy_, sg_uz_,
+      sg_w_, stg_off_, bad_;
+  Staging<R> stg_{};
+  long long stg_n_ = 0;
+  OverflowDev<R> ovf_{};
+  int ovf_cap_ = 0;
+  int n_items_ = 0, n_yee_ = 0, max_tx_ = 2, max_ty_ = 2;
+  BatchStatus *h_st_ = nullptr;
+  long long target_ = 0;
+  int sticky_ = ZPIC_OK;
+  int resorts_ = 0;
+  bool profiling_ = false;
+  std::vector<Timer<R>> timers_;
+  cudaGraphExec_t graph_exec_ = nullptr;
+};
+
+int make_batch(const zpic_config *cfgs, int n, zpic_batch **out) {
+  if (!out) return fail(ZPIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || n < 1) return fail(ZPIC_EINVAL, "no configs");
+  for (int i = 0; i < n; ++i) ZP_TRY(validate(&cfgs[i]));
+  for (int i = 1; i < n; ++i)
+    if (cfgs[i].precision != cfgs[0].precision)
+      return fail(ZPIC_EINVAL, "all sims of a batch share one precision");
+  std::unique_ptr<zpic_batch> b(new zpic_batch);
+  if (cfgs[0].precision == ZPIC_FP64)
+    b->impl.reset(new Batch<double>());
+  else
+    b->impl.reset(new Batch<float>());
+  int r = b->impl->init(cfgs, n);
+  if (r != ZPIC_OK) return r;
+  for (int i = 0; i < n; ++i) b->views.push_back(new zpic_sim{b.get(), i, false});
+  *out = b.release();
+  return ZPIC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+#define ZP_SIM(sim)                                               \
+  if (!(sim) || !(sim)->b) return fail(ZPIC_EINVAL, "NULL handle"); \
+  BatchBase *B = (sim)->b->impl.get();                            \
+  const int I = (sim)->index;
+
+extern "C" {
+
+int zpic_create(const zpic_config *cfg, zpic_sim **out) {
+  if (!out) return fail(ZPIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  zpic_batch *b = nullptr;
+  ZP_TRY(make_batch(cfg, 1, &b));
+  zpic_sim *s = b->views[0];
+  s->owns = true;
+  *out = s;
+  return ZPIC_OK;
+}
+
+int zpic_destroy(zpic_sim *sim) {
+  if (!sim || !sim->b) return fail(ZPIC_EINVAL, "NULL handle");
+  if (!sim->owns) return fail(ZPIC_EINVAL, "batch views are freed with the batch");
+  return zpic_batch_destroy(sim->b);
+}
+
+int zpic_step(zpic_sim *sim, int n) {
+  ZP_SIM(sim);
+  (void)I;
+  if (!sim->owns) return fail(ZPIC_EINVAL, "step a batch view with zpic_batch_step");
+  return B->step(n);
+}
+
+int zpic_sync(zpic_sim *sim) {
+  ZP_SIM(sim);
+  (void)I;
+  return B->sync();
+}
+
+int zpic_set_stream(zpic_sim *sim, void *stream) {
+  ZP_SIM(sim);
+  (void)I;
+  return B->set_stream(stream);
+}
+
+int zpic_get_fields_f32(zpic_sim *sim, int which, float *dst, size_t cap) {
+  ZP_SIM(sim);
+  return B->get_fields(I, which, dst, cap, 0);
+}
+
+int zpic_get_fields_f64(zpic_sim *sim, int which, double *dst, size_t cap) {
+  ZP_SIM(sim);
+  return B->get_fields(I, which, dst, cap, 1);
+}
+
+int zpic_set_fields_f64(zpic_sim *sim, int which, const double *src, size_t n) {
+  ZP_SIM(sim);
+  return B->set_fields_f64(I, which, src, n);
+}
+
+int zpic_num_particles(zpic_sim *sim, int species, int64_t *n) {
+  ZP_SIM(sim);
+  return B->num_particles(I, species, n);
+}
+
+int zpic_get_particles(zpic_sim *sim, int species, const zpic_particles *dst,
+                       size_t *n_written) {
+  ZP_SIM(sim);
+  return B->get_particles(I, species, dst, n_written);
+}
+
+int zpic_set_particles(zpic_sim *sim, int species, const zpic_particles *src) {
+  ZP_SIM(sim);
+  return B->set_particles(I, species, src);
+}
+
+int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
+                size_t *n_written) {
+  ZP_SIM(sim);
+  return B->energy(I, dst, cap, n_written);
+}
+
+int zpic_get_info(zpic_sim *sim, zpic_info *info) {
+  ZP_SIM(sim);
+  return B->info(I, info);
+}
+
+int zpic_get_tile_counts(zpic_sim *sim, int species, int32_t *dst, size_t cap) {
+  ZP_SIM(sim);
+  return B->tile_counts(I, species, dst, cap);
+}
+
+int zpic_profile_enable(zpic_sim *sim, int enable) {
+  ZP_SIM(sim);
+  (void)I;
+  return B->profile_enable(enable);
+}
+
+int zpic_profile_read(zpic_sim *sim, char *names, size_t name_len,
+                      double *ms_total, int32_t *launches, int cap, int *n,
+                      int reset) {
+  ZP_SIM(sim);
+  (void)I;
+  return B->profile_read(names, name_len, ms_total, launches, cap, n, reset);
+}
+
+int zpic_batch_create(const zpic_config *cfgs, int n, zpic_batch **out) {
+  return make_batch(cfgs, n, out);
+}
+
+int zpic_batch_step(zpic_batch *b, int n) {
+  if (!b) return fail(ZPIC_EINVAL, "NULL batch");
+  return b->impl->step(n);
+}
+
+int zpic_batch_sync(zpic_batch *b) {
+  if (!b) return fail(ZPIC_EINVAL, "NULL batch");
+  return b->impl->sync();
+}
+
+int zpic_batch_sim(zpic_batch *b, int i, zpic_sim **view) {
+  if (!b || !view) return fail(ZPIC_EINVAL, "NULL argument");
+  if (i < 0 || i >= (int)b->views.size()) return fail(ZPIC_EINVAL, "index");
+  *view = b->views[i];
+  return ZPIC_OK;
+}
+
+int zpic_batch_set_stream(zpic_batch *b, void *stream) {
+  if (!b) return fail(ZPIC_EINVAL, "NULL batch");
+  return b->impl->set_stream(stream);
+}
+
+int zpic_batch_profile_enable(zpic_batch *b, int enable) {
+  if (!b) return fail(ZPIC_EINVAL, "NULL batch");
+  return b->impl->profile_enable(enable);
+}
+
+int zpic_batch_destroy(zpic_batch *b) {
+  if (!b) return fail(ZPIC_EINVAL, "NULL batch");
+  for (zpic_sim *v : b->views) delete v;
+  b->views.clear();
+  b->impl.reset();
+  delete b;
+  return ZPIC_OK;
+}
+
+int zpic_set_allocator(zpic_alloc_fn alloc, zpic_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(ZPIC_EINVAL, "give both hooks or neither");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return ZPIC_OK;
+}
+
+const char *zpic_strerror(int code) {
+  switch (code) {
+    case ZPIC_OK: return "ok";
+    case ZPIC_EINVAL: return "invalid argument";
+    case ZPIC_ECFL: return "time step violates the Courant condition";
+    case ZPIC_ENOMEM: return "out of memory";
+    case ZPIC_ECUDA: return "CUDA error";
+    case ZPIC_EOVERFLOW: return "particle storage overflow";
+    case ZPIC_ENAN: return "non-finite value";
+    case ZPIC_ETIMEOUT: return "device wait timed out";
+    case ZPIC_ECAP: return "destination buffer too small";
+    case ZPIC_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+const char *zpic_last_error(void) { return g_last_error.c_str(); }
+
+int zpic_version(void) { return ZPIC_VERSION; }
+
+}  // extern "C"

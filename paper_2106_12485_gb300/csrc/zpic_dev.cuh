@@ -1,0 +1,130 @@
+// zpic_dev.cuh -- device-side data layout of the GB300 PIC library.
+//
+// One "batch" holds one or more independent simulations that advance in
+// lockstep.  Every kernel walks a work list of (simulation, tile) items and
+// reads the simulation's SimDev descriptor from device memory, so a single
+// simulation is simply a batch of one.
+//
+// HBM layout per simulation (R = float or double):
+//   fields: E[2][3], B[2][3], J[2][3] arrays of ny rows x ld (ld = nx padded
+//           to 128 bytes); copy (step & 1) is current, the Yee kernel
+//           writes copy (step & 1) ^ 1 (ping-pong, no halo races);
+//   particles, per species: SoA arrays ix, iy (int32), x, y, ux, uy, uz
+//           (R), optional w (R) and id (int32), cut into one segment per
+//           tile [off[t], off[t] + cap[t]) of which cnt[t] are live;
+//   outbox, per species: ob_cap slots per tile for particles that leave it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/zpic.h"
+
+namespace zp {
+
+constexpr int kMaxSpecies = ZPIC_MAX_SPECIES;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// BatchStatus::error bits
+constexpr int ERR_OVERFLOW = 1;  // particles parked in the overflow buffer
+constexpr int ERR_LOST = 2;      // overflow buffer full: particles dropped
+constexpr int ERR_NAN = 4;       // non-finite energy
+constexpr int ERR_STORE = 8;     // a stored particle lies outside its tile
+
+struct BatchStatus {
+  int step;         // completed steps
+  int error;        // ERR_* bits
+  int err_step;     // step that raised the first error (valid if error)
+  int ovf_count;    // entries claimed in the overflow buffer
+  int lost;         // particles dropped (overflow buffer full)
+  int blocks_done;  // ticket counter of the end-of-step kernel
+  int pad[2];
+};
+
+template <typename R>
+struct SpeciesDev {
+  R qm;          // charge-to-mass ratio
+  R hq;          // (q/m) dt / 2 : Boris half-kick factor
+  R qx, qy;      // q0 dx/dt, q0 dy/dt : Jx, Jy per unit cell displacement
+  R q0;          // charge of a weight-1 particle
+  double kin_scale;  // (q0 / (q/m)) dx dy : mass x cell area, weight 1
+  int *ix, *iy, *id;               // id may be null
+  R *x, *y, *ux, *uy, *uz, *w;     // w may be null (all weights 1)
+  int *off, *cap, *cnt;            // per tile
+  int ob_cap;                      // outbox slots per tile
+  int *ob_cnt;                     // per tile
+  int *ob_ix, *ob_iy, *ob_id;
+  R *ob_x, *ob_y, *ob_ux, *ob_uy, *ob_uz, *ob_w;
+  // moving-window injection of cold plasma on a lattice
+  int inj_ppc_x, inj_ppc_y;        // 0: no injection
+  double ramp_x0, ramp_len, n0;
+  long long id_base;
+};
+
+template <typename R>
+struct SimDev {
+  int nx, ny, ld;
+  int tx, ty, ntx, nty;        // particle tiles
+  int ybx, yby;                // Yee blocks in x, y
+  int open_x, moving_window;
+  int energy_every;
+  int nsp;
+  R dx, dy, dt;
+  R dt_dx, dt_dy;              // dt/dx, dt/dy (cells per unit velocity)
+  double dx_d, dy_d, dt_d;     // double values (window schedule, setup)
+  R *E[2][3], *B[2][3], *J[2][3];
+  double *part_kin;            // [ntiles][kMaxSpecies] kinetic partials
+  double *part_fld;            // [ybx*yby][2] field-energy partials
+  zpic_energy_rec *hist;       // energy history
+  int hist_cap;
+  int *hist_n;                 // records written
+  int *n_shift;                // window shifts done
+  int *removed;                // [kMaxSpecies] particles removed at edges
+  SpeciesDev<R> sp[kMaxSpecies];
+};
+
+// Particles that found no room (outbox or tile full) wait here until the
+// host re-sorts the batch.
+template <typename R>
+struct OverflowDev {
+  int cap;
+  int *sim, *species, *ix, *iy, *id;
+  R *x, *y, *ux, *uy, *uz, *w;
+};
+
+// --- small device helpers --------------------------------------------------
+
+__device__ __forceinline__ int wrap1(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Window schedule: shift after step `step` if (step+1) dt >= (n_shift+1) dx.
+// Evaluated in double exactly as written so every kernel (and any other
+// implementation of the same rule) takes the same decision.
+template <typename R>
+__device__ __forceinline__ bool shift_due(const SimDev<R> &S, int step,
+                                          int n_shift) {
+  return S.moving_window &&
+         ((double)(step + 1) * S.dt_d >= (double)(n_shift + 1) * S.dx_d);
+}
+
+__device__ __forceinline__ bool frozen(const BatchStatus *st, int step) {
+  // after an error in an earlier step, later steps are held back until the
+  // host has recovered (the step counter stops, the host re-runs them)
+  return st->error != 0 && st->err_step < step;
+}
+
+// --- SplitMix64 (Steele, Lea & Flood 2014), counter form -------------------
+
+__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// k-th output (k >= 1) of a SplitMix64 generator seeded with s
+__host__ __device__ __forceinline__ uint64_t sm_out(uint64_t s, uint64_t k) {
+  return sm_mix(s + k * 0x9E3779B97F4A7C15ull);
+}
+
+}  // namespace zp

@@ -1,0 +1,99 @@
+// zpic_kernels.h -- host-side launchers of the CUDA kernels (all async on
+// the given stream).
+#pragma once
+
+#include "zpic_dev.cuh"
+
+namespace zp {
+
+// Yee blocks: 32 x 8 cells per CTA
+constexpr int kYeeX = 32;
+constexpr int kYeeY = 8;
+
+template <typename R>
+size_t push_smem_bytes(int tx, int ty);
+
+// Sets the push kernel's dynamic shared-memory limit (call before launching
+// or capturing it).
+template <typename R>
+cudaError_t prepare_push_deposit(int max_tx, int max_ty);
+
+// Stages 1-3 over all (sim, tile) items.
+template <typename R>
+cudaError_t launch_push_deposit(const SimDev<R> *sims, const int2 *items,
+                                int n_items, int max_tx, int max_ty,
+                                BatchStatus *st, const OverflowDev<R> &ovf,
+                                cudaStream_t stream);
+
+// Stage 4 (B half, E, B half) over all (sim, yee block) items; writes the
+// other field copy (shifted one cell when the window moves), zeroes the
+// other J copy, field-energy partials on energy steps.
+template <typename R>
+cudaError_t launch_yee(const SimDev<R> *sims, const int2 *items, int n_items,
+                       BatchStatus *st, cudaStream_t stream);
+
+// Moves outbox particles into their new tiles, injects the window column.
+template <typename R>
+cudaError_t launch_migrate(const SimDev<R> *sims, const int2 *items,
+                           int n_items, BatchStatus *st,
+                           const OverflowDev<R> &ovf, cudaStream_t stream);
+
+// Energy records, window counter, step counter.
+template <typename R>
+cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
+                            BatchStatus *st, cudaStream_t stream);
+
+// Laser fields (Sec. 4.1) added to the current E, B copy of one sim.
+struct LaserParams {
+  double E0, omega0, w0, fwhm, x0, yc;
+};
+template <typename R>
+cudaError_t launch_laser(const SimDev<R> *sim_dev, int nx, int ny,
+                         LaserParams lp, cudaStream_t stream);
+
+// Initial load of species s of one sim (counter-based SplitMix64).
+struct LoadParams {
+  int species;
+  uint64_t key;                 // generator key of (seed, sim, species)
+  int ppc_x, ppc_y, lattice;
+  double u_th[3], u_fl[3];
+  int profile;                  // ZPIC_PROFILE_*
+  double x0, x1, n0;
+  int col_lo, col_hi;           // loaded cell columns [col_lo, col_hi)
+};
+template <typename R>
+cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
+                             LoadParams lp, cudaStream_t stream);
+
+// Staging SoA used by set/get particles and re-sorting.
+template <typename R>
+struct Staging {
+  int *ix, *iy, *id, *tile;
+  R *x, *y, *ux, *uy, *uz, *w;
+};
+
+// tile of each staged particle + per-tile counts; bad[0] counts particles
+// outside the grid or with offsets outside [0, 1)
+template <typename R>
+cudaError_t launch_bin_count(Staging<R> in, long long n, int nx, int ny,
+                             int tx, int ty, int ntx, int *counts, int *bad,
+                             cudaStream_t stream);
+// scatters staged particles into the species' tile store (cnt used as
+// cursor, must be zero); ids default to the index when in.id is null
+template <typename R>
+cudaError_t launch_bin_scatter(Staging<R> in, long long n,
+                               SpeciesDev<R> sp_host_copy, int has_w,
+                               int has_id, cudaStream_t stream);
+// compacts the tile store into a contiguous staging copy at dst_off[t]
+template <typename R>
+cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int ntiles,
+                           const long long *dst_off, Staging<R> out,
+                           cudaStream_t stream);
+// appends the overflow entries of (sim, species) to staging at *n_io
+template <typename R>
+cudaError_t launch_take_overflow(OverflowDev<R> ovf, int n_entries, int sim,
+                                 int species, Staging<R> out,
+                                 long long out_base, int *n_taken,
+                                 cudaStream_t stream);
+
+}  // namespace zp

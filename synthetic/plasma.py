@@ -165,7 +165,7 @@ def batch_specs(n_sims=256, seed=DEFAULT_SEED):
         k = 2 + int(uni[2] * 7)               # 2..8
         u_th = 0.01 + 0.19 * uni[3]
         drift = 0.1 + 0.2 * uni[4]
-        specs.append({"nx": nx, "ny": ny, "ppc": k, "u_th": float(u_th),
+        specs.append({"nx": nx, "ny": ny, "ppc_side": k, "u_th": float(u_th),
                       "kind": "thermal" if i % 2 == 0 else "clouds",
                       "drift": float(drift)})
     return specs
