@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(kThreads)
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
 
+  const int nxt = (step + 1) & 1;  // the copy the push kernel just wrote
   for (int s = 0; s < S.nsp; ++s) {
     const SpeciesDev<R> &P = S.sp[s];
+    const Planes<R> &O = P.buf[nxt];
     __syncthreads();
     if (threadIdx.x == 0) cursor = 0;
     __syncthreads();
@@ -123,19 +125,19 @@ __global__ void __launch_bounds__(kThreads)
         if (!mine) continue;
         const size_t e = ob + k;
         const int d = n_stay + wb + __popc(bal & lt);
-        const R w = P.w ? P.ob_w[e] : R(1);
-        const int id = P.id ? P.ob_id[e] : 0;
+        const R w = O.w ? P.ob_w[e] : R(1);
+        const int id = O.id ? P.ob_id[e] : 0;
         if (d < cap) {
           const size_t t = base + d;
-          P.ix[t] = ix;
-          P.iy[t] = iy;
-          P.x[t] = P.ob_x[e];
-          P.y[t] = P.ob_y[e];
-          P.ux[t] = P.ob_ux[e];
-          P.uy[t] = P.ob_uy[e];
-          P.uz[t] = P.ob_uz[e];
-          if (P.w) P.w[t] = w;
-          if (P.id) P.id[t] = id;
+          O.ix[t] = ix;
+          O.iy[t] = iy;
+          O.x[t] = P.ob_x[e];
+          O.y[t] = P.ob_y[e];
+          O.ux[t] = P.ob_ux[e];
+          O.uy[t] = P.ob_uy[e];
+          O.uz[t] = P.ob_uz[e];
+          if (O.w) O.w[t] = w;
+          if (O.id) O.id[t] = id;
         } else {
           park(ovf, st, step, it.x, s, ix, iy, id, P.ob_x[e], P.ob_y[e],
                P.ob_ux[e], P.ob_uy[e], P.ob_uz[e], w);
@@ -167,15 +169,15 @@ __global__ void __launch_bounds__(kThreads)
           const int d = n_stay + wb + __popc(bal & lt);
           if (d < cap) {
             const size_t t = base + d;
-            P.ix[t] = i;
-            P.iy[t] = j;
-            P.x[t] = x;
-            P.y[t] = y;
-            P.ux[t] = R(0);
-            P.uy[t] = R(0);
-            P.uz[t] = R(0);
-            if (P.w) P.w[t] = (R)dens;
-            if (P.id) P.id[t] = id;
+            O.ix[t] = i;
+            O.iy[t] = j;
+            O.x[t] = x;
+            O.y[t] = y;
+            O.ux[t] = R(0);
+            O.uy[t] = R(0);
+            O.uz[t] = R(0);
+            if (O.w) O.w[t] = (R)dens;
+            if (O.id) O.id[t] = id;
           } else {
             park(ovf, st, step, it.x, s, i, j, id, x, y, R(0), R(0), R(0),
                  (R)dens);
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(kThreads)
     init_load_kernel(const SimDev<R> *__restrict__ sim, LoadParams lp) {
   const SimDev<R> &S = *sim;
   const SpeciesDev<R> &P = S.sp[lp.species];
+  const Planes<R> &O = P.buf[lp.buf];
   const int tile = blockIdx.x;
   const int tcx = tile % S.ntx, tcy = tile / S.ntx;
   const int x0 = tcx * S.tx, y0 = tcy * S.ty;
@@ -259,15 +262,15 @@ __global__ void __launch_bounds__(kThreads)
       w = xc < lp.x0 + lp.x1 ? lp.n0 * (xc - lp.x0) / lp.x1 : lp.n0;
     }
     const size_t t = base + q;
-    P.ix[t] = ix;
-    P.iy[t] = iy;
-    P.x[t] = (R)x;
-    P.y[t] = (R)y;
-    P.ux[t] = (R)u[0];
-    P.uy[t] = (R)u[1];
-    P.uz[t] = (R)u[2];
-    if (P.w) P.w[t] = (R)w;
-    if (P.id) P.id[t] = (int)(c * ppc + k);
+    O.ix[t] = ix;
+    O.iy[t] = iy;
+    O.x[t] = (R)x;
+    O.y[t] = (R)y;
+    O.ux[t] = (R)u[0];
+    O.uy[t] = (R)u[1];
+    O.uz[t] = (R)u[2];
+    if (O.w) O.w[t] = (R)w;
+    if (O.id) O.id[t] = (int)(c * ppc + k);
   }
 }
 
@@ -317,33 +320,35 @@ cudaError_t launch_bin_count(Staging<R> in, long long n, int nx, int ny,
 
 template <typename R>
 __global__ void bin_scatter_kernel(Staging<R> in, long long n, SpeciesDev<R> P,
-                                   int has_w, int has_id) {
+                                   int b, int has_w, int has_id) {
+  const Planes<R> &O = P.buf[b];
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const int t = in.tile[p];
     if (t < 0) continue;
     const int slot = atomicAdd(&P.cnt[t], 1);
     const size_t d = (size_t)P.off[t] + slot;
-    P.ix[d] = in.ix[p];
-    P.iy[d] = in.iy[p];
-    P.x[d] = in.x[p];
-    P.y[d] = in.y[p];
-    P.ux[d] = in.ux[p];
-    P.uy[d] = in.uy[p];
-    P.uz[d] = in.uz[p];
-    if (P.w) P.w[d] = has_w ? in.w[p] : R(1);
-    if (P.id) P.id[d] = has_id ? in.id[p] : (int)p;
+    O.ix[d] = in.ix[p];
+    O.iy[d] = in.iy[p];
+    O.x[d] = in.x[p];
+    O.y[d] = in.y[p];
+    O.ux[d] = in.ux[p];
+    O.uy[d] = in.uy[p];
+    O.uz[d] = in.uz[p];
+    if (O.w) O.w[d] = has_w ? in.w[p] : R(1);
+    if (O.id) O.id[d] = has_id ? in.id[p] : (int)p;
   }
 }
 
 template <typename R>
 cudaError_t launch_bin_scatter(Staging<R> in, long long n, SpeciesDev<R> sp,
-                               int has_w, int has_id, cudaStream_t stream) {
+                               int b, int has_w, int has_id,
+                               cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   const int grid = (int)((n + kThreads - 1) / kThreads < 152 * 16
                              ? (n + kThreads - 1) / kThreads
                              : 152 * 16);
-  bin_scatter_kernel<R><<<grid, kThreads, 0, stream>>>(in, n, sp, has_w,
+  bin_scatter_kernel<R><<<grid, kThreads, 0, stream>>>(in, n, sp, b, has_w,
                                                        has_id);
   return cudaGetLastError();
 }
@@ -352,30 +357,32 @@ cudaError_t launch_bin_scatter(Staging<R> in, long long n, SpeciesDev<R> sp,
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    compact_kernel(SpeciesDev<R> P, const long long *dst_off, Staging<R> out) {
+    compact_kernel(SpeciesDev<R> P, int b, const long long *dst_off,
+                   Staging<R> out) {
+  const Planes<R> &I = P.buf[b];
   const int t = blockIdx.x;
   const int n = P.cnt[t];
   const size_t src = (size_t)P.off[t];
   const size_t dst = (size_t)dst_off[t];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    out.ix[dst + k] = P.ix[src + k];
-    out.iy[dst + k] = P.iy[src + k];
-    out.x[dst + k] = P.x[src + k];
-    out.y[dst + k] = P.y[src + k];
-    out.ux[dst + k] = P.ux[src + k];
-    out.uy[dst + k] = P.uy[src + k];
-    out.uz[dst + k] = P.uz[src + k];
-    out.w[dst + k] = P.w ? P.w[src + k] : R(1);
-    out.id[dst + k] = P.id ? P.id[src + k] : 0;
+    out.ix[dst + k] = I.ix[src + k];
+    out.iy[dst + k] = I.iy[src + k];
+    out.x[dst + k] = I.x[src + k];
+    out.y[dst + k] = I.y[src + k];
+    out.ux[dst + k] = I.ux[src + k];
+    out.uy[dst + k] = I.uy[src + k];
+    out.uz[dst + k] = I.uz[src + k];
+    out.w[dst + k] = I.w ? I.w[src + k] : R(1);
+    out.id[dst + k] = I.id ? I.id[src + k] : 0;
   }
 }
 
 template <typename R>
-cudaError_t launch_compact(SpeciesDev<R> sp, int ntiles,
+cudaError_t launch_compact(SpeciesDev<R> sp, int b, int ntiles,
                            const long long *dst_off, Staging<R> out,
                            cudaStream_t stream) {
   if (ntiles == 0) return cudaSuccess;
-  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, dst_off, out);
+  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, b, dst_off, out);
   return cudaGetLastError();
 }
 
@@ -422,9 +429,9 @@ cudaError_t launch_take_overflow(OverflowDev<R> ovf, int n_entries, int sim,
                                            int, int, int, int *, int *,       \
                                            cudaStream_t);                     \
   template cudaError_t launch_bin_scatter<R>(Staging<R>, long long,           \
-                                             SpeciesDev<R>, int, int,         \
+                                             SpeciesDev<R>, int, int, int,    \
                                              cudaStream_t);                   \
-  template cudaError_t launch_compact<R>(SpeciesDev<R>, int,                  \
+  template cudaError_t launch_compact<R>(SpeciesDev<R>, int, int,             \
                                          const long long *, Staging<R>,       \
                                          cudaStream_t);                       \
   template cudaError_t launch_take_overflow<R>(OverflowDev<R>, int, int, int, \

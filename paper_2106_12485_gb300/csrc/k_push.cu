@@ -12,10 +12,11 @@
 //     relativistic Boris rotation, move by dt u/gamma (at most one cell,
 //     CFL), split of the straight path at the cell faces it crosses and
 //     accumulation of each segment's current into the shared J tile;
-//  3. writes particles that stay in the tile back to the front of the
-//     segment (stable in-place compaction: ballot + prefix per warp, warp
-//     totals through shared memory) and particles that leave to the tile's
-//     outbox; particles leaving an open boundary are dropped;
+//  3. writes particles that stay in the tile to the tile's segment of the
+//     other copy of the store (each warp claims a run of slots with one
+//     shared-memory atomic, so warps never wait for each other) and
+//     particles that leave to the tile's outbox; particles leaving an open
+//     boundary are dropped;
 //  4. adds the shared J tile (interior and guard cells) to the global J
 //     with one reduction per cell (periodic images folded here).
 // Traffic per particle: one read and one write of its SoA record.
@@ -58,39 +59,76 @@ __device__ __forceinline__ int axis_cross(R o1, R &of, R &oe) {
   return 0;
 }
 
-// One straight segment inside cell (ci, cj) (tile-local), from (xa, ya) to
-// (xb, yb) in that cell's offsets, covering fraction f of the step.
-// js: three planes of JP values, row length JW, origin at cell (-1, -1).
+// Shared current tile.  FP32: each value is an exact fixed-point sum held
+// in two 32-bit words, hi = sum floor(t) and lo = sum round(frac(t) 2^14),
+// for contributions t = c 2^16 with |c| <= 1 unit (value = hi 2^14 + lo in
+// units of 2^-30).  Integer shared atomics are native (float ones are not),
+// and integer sums do not depend on the order of the adds.  The split is
+// exact as long as one word receives fewer than 2^18 adds per step and the
+// net sum stays below 2^15 units.  FP64: plain double atomics.
 template <typename R>
-__device__ __forceinline__ void dep_seg(R *js, int JW, int JP, int ci, int cj,
-                                        R xa, R ya, R xb, R yb, R f, R qx,
-                                        R qy, R qz) {
+struct TileJ;
+
+template <>
+struct TileJ<float> {
+  int *hi;
+  unsigned *lo;
+  __device__ __forceinline__ void add(int idx, float t) const {
+    const float fh = floorf(t);
+    atomicAdd(hi + idx, (int)fh);
+    atomicAdd(lo + idx, (unsigned)__float2int_rn((t - fh) * 16384.0f));
+  }
+  __device__ __forceinline__ bool nonzero(int idx) const {
+    return (hi[idx] | (int)lo[idx]) != 0;
+  }
+  __device__ __forceinline__ double value(int idx) const {
+    return (double)hi[idx] * 16384.0 + (double)lo[idx];
+  }
+  __device__ __forceinline__ void zero(int n) const {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      hi[k] = 0;
+      lo[k] = 0u;
+    }
+  }
+};
+
+template <>
+struct TileJ<double> {
+  double *v;
+  __device__ __forceinline__ void add(int idx, double t) const {
+    atomicAdd(v + idx, t);
+  }
+  __device__ __forceinline__ bool nonzero(int idx) const { return v[idx] != 0.0; }
+  __device__ __forceinline__ double value(int idx) const { return v[idx]; }
+  __device__ __forceinline__ void zero(int n) const {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) v[k] = 0.0;
+  }
+};
+
+// One straight segment inside cell (ci, cj) (tile-local), from (xa, ya) to
+// (xb, yb) in that cell's offsets, covering fraction f of the step; qx, qy,
+// qz are the particle's deposit factors.  Planes of JP values, row length
+// JW, origin at cell (-1, -1).
+template <typename R>
+__device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
+                                        int ci, int cj, R xa, R ya, R xb, R yb,
+                                        R f, R qx, R qy, R qz) {
   const R ddx = xb - xa, ddy = yb - ya;
   const R xm = R(0.5) * (xa + xb), ym = R(0.5) * (ya + yb);
   const int b = (cj + 1) * JW + (ci + 1);
   const R ax = qx * ddx, ay = qy * ddy, az = qz * f;
   const R c = ddx * ddy * R(1.0 / 12.0);
-  R *jx = js, *jy = js + JP, *jz = js + 2 * JP;
-  atomicAdd(jx + b, ax * (R(1) - ym));
-  atomicAdd(jx + b + JW, ax * ym);
-  atomicAdd(jy + b, ay * (R(1) - xm));
-  atomicAdd(jy + b + 1, ay * xm);
-  atomicAdd(jz + b, az * ((R(1) - xm) * (R(1) - ym) + c));
-  atomicAdd(jz + b + 1, az * (xm * (R(1) - ym) - c));
-  atomicAdd(jz + b + JW, az * ((R(1) - xm) * ym - c));
-  atomicAdd(jz + b + JW + 1, az * (xm * ym + c));
-}
-
-template <typename R>
-__device__ __forceinline__ R field_at(const SimDev<R> &S, const R *f, int gi,
-                                      int gj) {
-  gj = wrap1(gj, S.ny);
-  if (S.open_x) {
-    if (gi < 0 || gi >= S.nx) return R(0);
-  } else {
-    gi = wrap1(gi, S.nx);
-  }
-  return f[(size_t)gj * S.ld + gi];
+  // charge flux through the x faces (i+1/2, j), (i+1/2, j+1)
+  J.add(b, ax * (R(1) - ym));
+  J.add(b + JW, ax * ym);
+  // through the y faces (i, j+1/2), (i+1, j+1/2)
+  J.add(JP + b, ay * (R(1) - xm));
+  J.add(JP + b + 1, ay * xm);
+  // q vz times the path-averaged bilinear weights of the four nodes
+  J.add(2 * JP + b, az * ((R(1) - xm) * (R(1) - ym) + c));
+  J.add(2 * JP + b + 1, az * (xm * (R(1) - ym) - c));
+  J.add(2 * JP + b + JW, az * ((R(1) - xm) * ym - c));
+  J.add(2 * JP + b + JW + 1, az * (xm * ym + c));
 }
 
 template <typename R>
@@ -110,221 +148,256 @@ __device__ __forceinline__ void block_sum_store(double v, double *dst,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ __forceinline__ R fdiv(R a, R b);
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <>
+__device__ __forceinline__ double fdiv<double>(double a, double b) {
+  return a / b;
+}
+
+// kBatch = false: one simulation, its descriptor passed as a grid-constant
+// kernel parameter (fields read from the constant bank, no registers held);
+// kBatch = true: descriptors of many simulations read from device memory.
+template <typename R, bool kBatch>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
     push_deposit_kernel(const SimDev<R> *__restrict__ sims,
+                        const __grid_constant__ SimDev<R> one,
                         const int2 *__restrict__ items, BatchStatus *st,
                         OverflowDev<R> ovf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int wcnt[2][kWarps][2];
+  __shared__ int s_slots[2];  // stayers written, leavers written
   __shared__ double red[kWarps];
 
   const int step = st->step;
   if (frozen(st, step)) return;
   const int2 it = items[blockIdx.x];
-  const SimDev<R> &S = sims[it.x];
+  const SimDev<R> &S = kBatch ? sims[it.x] : one;
   const int tile = it.y;
+  const int nx = S.nx, ny = S.ny, ld = S.ld, TX = S.tx, TY = S.ty;
+  const int open_x = S.open_x, nsp = S.nsp;
+  const R dt_dx = S.dt_dx, dt_dy = S.dt_dy;
   const int tcx = tile % S.ntx, tcy = tile / S.ntx;
-  const int x0 = tcx * S.tx, y0 = tcy * S.ty;
-  const int tw = min(S.tx, S.nx - x0), th = min(S.ty, S.ny - y0);
+  const int x0 = tcx * TX, y0 = tcy * TY;
+  const int tw = min(TX, nx - x0), th = min(TY, ny - y0);
   const int cur = step & 1;
 
   // shared layout: 6 field planes (FW x FH) then 3 current planes (JW x JH)
-  const int FW = S.tx + 2, FH = S.ty + 2, FP = FW * FH;
-  const int JW = S.tx + 3, JH = S.ty + 3, JP = JW * JH;
+  const int FW = TX + 2, FH = TY + 2, FP = FW * FH;
+  const int JW = TX + 3, JH = TY + 3, JP = JW * JH;
   R *fs = reinterpret_cast<R *>(smem_raw);
-  R *js = fs + 6 * FP;
-
-  {
-    const R *src[6] = {S.E[cur][0], S.E[cur][1], S.E[cur][2],
-                       S.B[cur][0], S.B[cur][1], S.B[cur][2]};
-    for (int k = threadIdx.x; k < 6 * FP; k += blockDim.x) {
-      const int c = k / FP, r = k - c * FP;
-      const int lj = r / FW, li = r - lj * FW;
-      fs[k] = field_at(S, src[c], x0 - 1 + li, y0 - 1 + lj);
-    }
-    for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) js[k] = R(0);
+  TileJ<R> jt;
+  if constexpr (sizeof(R) == 4) {
+    jt.hi = reinterpret_cast<int *>(fs + 6 * FP);
+    jt.lo = reinterpret_cast<unsigned *>(jt.hi + 3 * JP);
+  } else {
+    jt.v = reinterpret_cast<double *>(fs + 6 * FP);
   }
+
+  for (int k = threadIdx.x; k < 6 * FP; k += blockDim.x) {
+    const int c = k / FP, r = k - c * FP;
+    const int lj = r / FW, li = r - lj * FW;
+    const R *src = c < 3 ? S.E[cur][c] : S.B[cur][c - 3];
+    int gi = x0 - 1 + li;
+    const int gj = wrap1(y0 - 1 + lj, ny);
+    R v = R(0);
+    if (open_x) {
+      if (gi >= 0 && gi < nx) v = src[(size_t)gj * ld + gi];
+    } else {
+      gi = wrap1(gi, nx);
+      v = src[(size_t)gj * ld + gi];
+    }
+    fs[k] = v;
+  }
+  jt.zero(3 * JP);
   const int nsh = S.moving_window ? *S.n_shift : 0;
   const int shift = shift_due(S, step, nsh) ? 1 : 0;
   const bool do_energy =
       S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
-  __syncthreads();
 
   const R *Ex = fs, *Ey = fs + FP, *Ez = fs + 2 * FP;
   const R *Bx = fs + 3 * FP, *By = fs + 4 * FP, *Bz = fs + 5 * FP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  int chunk = 0;
 
-  for (int s = 0; s < S.nsp; ++s) {
+  for (int s = 0; s < nsp; ++s) {
     const SpeciesDev<R> &P = S.sp[s];
+    const Planes<R> &I = P.buf[cur];
+    const Planes<R> &O = P.buf[cur ^ 1];
+    const R hq = P.hq, qx0 = P.dq[0], qy0 = P.dq[1], q00 = P.dq[2];
     const int n = P.cnt[tile];
-    const size_t base = (size_t)P.off[tile];
-    const size_t obase = (size_t)tile * P.ob_cap;
-    int n_stay = 0, n_out = 0, n_removed = 0;
+    const int base = P.off[tile];
+    const int ob_cap = P.ob_cap;
+    if (threadIdx.x == 0) {
+      s_slots[0] = 0;
+      s_slots[1] = 0;
+    }
+    __syncthreads();  // also: fields staged, J tile zeroed
+    int n_removed = 0;
     R kin = R(0);
-    for (int c0 = 0; c0 < n; c0 += blockDim.x, ++chunk) {
-      const int k = c0 + threadIdx.x;
+    // warps work independently on chunks of 32 particles: no block barrier
+    // inside the loop; each warp claims its output slots with one atomic
+    for (int c0 = warp * 32; c0 < n; c0 += blockDim.x) {
+      const int k = c0 + lane;
       const bool valid = k < n;
-      bool stay = false, leave = false;
-      int nix = 0, niy = 0, pid = 0;
-      R xf = R(0), yf = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(1);
+      // invalid lanes carry a particle at rest in the tile's first cell and
+      // never deposit or store
+      int ix = x0, iy = y0, pid = 0;
+      R x = R(0.5), y = R(0.5), ux = R(0), uy = R(0), uz = R(0), w = R(1);
       if (valid) {
-        const size_t p = base + k;
-        const int ix = P.ix[p], iy = P.iy[p];
-        const R x = P.x[p], y = P.y[p];
-        ux = P.ux[p];
-        uy = P.uy[p];
-        uz = P.uz[p];
-        if (P.w) w = P.w[p];
-        if (P.id) pid = P.id[p];
-        int lx = ix - x0, ly = iy - y0;
-        if ((unsigned)lx >= (unsigned)tw || (unsigned)ly >= (unsigned)th) {
-          // never produced by the library's own kernels: record and keep
-          // the shared-memory accesses inside the tile
-          atomicOr(&st->error, ERR_STORE);
-          atomicMin(&st->err_step, step);
-          lx = min(max(lx, 0), tw - 1);
-          ly = min(max(ly, 0), th - 1);
-        }
+        const int p = base + k;
+        ix = __ldcs(I.ix + p);
+        iy = __ldcs(I.iy + p);
+        x = __ldcs(I.x + p);
+        y = __ldcs(I.y + p);
+        ux = __ldcs(I.ux + p);
+        uy = __ldcs(I.uy + p);
+        uz = __ldcs(I.uz + p);
+        if (I.w) w = __ldcs(I.w + p);
+        if (I.id) pid = __ldcs(I.id + p);
+      }
+      int lx = ix - x0, ly = iy - y0;
+      if ((unsigned)lx >= (unsigned)tw || (unsigned)ly >= (unsigned)th) {
+        // never produced by the library's own kernels: record it and keep
+        // the shared-memory accesses inside the tile
+        atomicOr(&st->error, ERR_STORE);
+        atomicMin(&st->err_step, step);
+        lx = min(max(lx, 0), tw - 1);
+        ly = min(max(ly, 0), th - 1);
+      }
 
-        // ---- stage 1: bilinear gather on the staggered grid ----
-        // node-centred axis: cell l, weight o; half-staggered axis: cell
-        // l-1 with weight o+1/2 if o < 1/2, else cell l with weight o-1/2
-        const bool xl = x < R(0.5), yl = y < R(0.5);
-        const int hx = xl ? lx - 1 : lx, hy = yl ? ly - 1 : ly;
-        const R whx = xl ? x + R(0.5) : x - R(0.5);
-        const R why = yl ? y + R(0.5) : y - R(0.5);
-        const int b_nn = (ly + 1) * FW + (lx + 1);
-        const int b_hn = (ly + 1) * FW + (hx + 1);
-        const int b_nh = (hy + 1) * FW + (lx + 1);
-        const int b_hh = (hy + 1) * FW + (hx + 1);
+      // ---- stage 1: bilinear gather on the staggered grid ----
+      // node-centred axis: cell l, weight o; half-staggered axis: cell l-1
+      // with weight o+1/2 if o < 1/2, else cell l with weight o-1/2
+      const bool xl = x < R(0.5), yl = y < R(0.5);
+      const int hx = xl ? lx - 1 : lx, hy = yl ? ly - 1 : ly;
+      const R whx = xl ? x + R(0.5) : x - R(0.5);
+      const R why = yl ? y + R(0.5) : y - R(0.5);
+      const int b_nn = (ly + 1) * FW + (lx + 1);
+      const int b_hn = (ly + 1) * FW + (hx + 1);
+      const int b_nh = (hy + 1) * FW + (lx + 1);
+      const int b_hh = (hy + 1) * FW + (hx + 1);
 #define ZP_BILIN(F, b, wx, wy)                                               \
   ((R(1) - (wy)) * ((R(1) - (wx)) * (F)[b] + (wx) * (F)[(b) + 1]) +          \
    (wy) * ((R(1) - (wx)) * (F)[(b) + FW] + (wx) * (F)[(b) + FW + 1]))
-        const R ex = ZP_BILIN(Ex, b_hn, whx, y);
-        const R ey = ZP_BILIN(Ey, b_nh, x, why);
-        const R ez = ZP_BILIN(Ez, b_nn, x, y);
-        const R bx = ZP_BILIN(Bx, b_nh, x, why);
-        const R by = ZP_BILIN(By, b_hn, whx, y);
-        const R bz = ZP_BILIN(Bz, b_hh, whx, why);
+      const R ex = ZP_BILIN(Ex, b_hn, whx, y);
+      const R ey = ZP_BILIN(Ey, b_nh, x, why);
+      const R ez = ZP_BILIN(Ez, b_nn, x, y);
+      const R bx = ZP_BILIN(Bx, b_nh, x, why);
+      const R by = ZP_BILIN(By, b_hn, whx, y);
+      const R bz = ZP_BILIN(Bz, b_hh, whx, why);
 #undef ZP_BILIN
 
-        // ---- stage 2: relativistic Boris ----
-        const R h = P.hq;
-        const R umx = ux + h * ex, umy = uy + h * ey, umz = uz + h * ez;
-        const R rg = rsqrt_r<R>(R(1) + umx * umx + umy * umy + umz * umz);
-        const R tx = h * bx * rg, ty = h * by * rg, tz = h * bz * rg;
-        const R sf = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
-        const R upx = umx + (umy * tz - umz * ty);
-        const R upy = umy + (umz * tx - umx * tz);
-        const R upz = umz + (umx * ty - umy * tx);
-        ux = umx + sf * (upy * tz - upz * ty) + h * ex;
-        uy = umy + sf * (upz * tx - upx * tz) + h * ey;
-        uz = umz + sf * (upx * ty - upy * tx) + h * ez;
+      // ---- stage 2: relativistic Boris ----
+      const R umx = ux + hq * ex, umy = uy + hq * ey, umz = uz + hq * ez;
+      const R rg = rsqrt_r<R>(R(1) + umx * umx + umy * umy + umz * umz);
+      const R tx = hq * bx * rg, ty = hq * by * rg, tz = hq * bz * rg;
+      const R sf = fdiv<R>(R(2), R(1) + tx * tx + ty * ty + tz * tz);
+      const R upx = umx + (umy * tz - umz * ty);
+      const R upy = umy + (umz * tx - umx * tz);
+      const R upz = umz + (umx * ty - umy * tx);
+      ux = umx + sf * (upy * tz - upz * ty) + hq * ex;
+      uy = umy + sf * (upz * tx - upx * tz) + hq * ey;
+      uz = umz + sf * (upx * ty - upy * tx) + hq * ez;
 
-        // ---- stage 2b: move ----
-        const R u2 = ux * ux + uy * uy + uz * uz;
-        const R rgn = rsqrt_r<R>(R(1) + u2);
-        if (do_energy) kin += w * u2 / (R(1) / rgn + R(1));  // w (gamma-1)
-        R x1 = x + S.dt_dx * ux * rgn;
-        R y1 = y + S.dt_dy * uy * rgn;
-        const int di = axis_cross(x1, xf, x1);
-        const int dj = axis_cross(y1, yf, y1);
+      // ---- stage 2b: move (at most one cell, CFL) ----
+      const R u2 = ux * ux + uy * uy + uz * uz;
+      const R rgn = rsqrt_r<R>(R(1) + u2);
+      if (do_energy && valid) kin += w * u2 * fdiv<R>(rgn, R(1) + rgn);
+      R x1 = x + dt_dx * ux * rgn;
+      R y1 = y + dt_dy * uy * rgn;
+      R xf, yf;
+      const int di = axis_cross(x1, xf, x1);
+      const int dj = axis_cross(y1, yf, y1);
 
-        // ---- stage 3: charge-conserving deposit, path split at faces ----
-        const R qx = P.qx * w, qy = P.qy * w, qz = P.q0 * w * uz * rgn;
-        if (di == 0 && dj == 0) {
-          dep_seg(js, JW, JP, lx, ly, x, y, xf, yf, R(1), qx, qy, qz);
-        } else if (dj == 0) {
-          const R xb = di > 0 ? R(1) : R(0);
-          const R sx = (xb - x) / (x1 - x);
-          const R yc = y + sx * (y1 - y);
-          dep_seg(js, JW, JP, lx, ly, x, y, xb, yc, sx, qx, qy, qz);
-          dep_seg(js, JW, JP, lx + di, ly, xb - R(di), yc, xf, yf, R(1) - sx,
+      // ---- stage 3: charge-conserving deposit ----
+      // The straight path from (x, y) to (x1, y1) (start-cell frame) is cut
+      // where it meets the x face xb (parameter sx) and the y face yb (sy);
+      // s1 = min, s2 = max (an exact tie counts as x first).  Segment 1 lies
+      // in the start cell, segment 2 in the cell entered at s1, segment 3 in
+      // the final cell; each is written in its own cell's frame and the last
+      // one ends at the stored offsets (xf, yf).  Empty segments are skipped
+      // per lane; a warp skips a segment that none of its lanes needs.
+      const R qx = qx0 * w, qy = qy0 * w, qz = q00 * w * uz * rgn;
+      const R xb = di > 0 ? R(1) : R(0);
+      const R yb = dj > 0 ? R(1) : R(0);
+      const R sx = di ? fdiv<R>(xb - x, x1 - x) : R(1);
+      const R sy = dj ? fdiv<R>(yb - y, y1 - y) : R(1);
+      const bool xfirst = sx <= sy;
+      const R s1 = xfirst ? sx : sy, s2 = xfirst ? sy : sx;
+      const R y_sx = y + sx * (y1 - y);  // where the path meets the x face
+      const R x_sy = x + sy * (x1 - x);  // where it meets the y face
+      const bool cut = di != 0 || dj != 0;
+      const bool two = di != 0 && dj != 0;
+      {
+        const R bx1 = cut ? (xfirst ? xb : x_sy) : xf;
+        const R by1 = cut ? (xfirst ? y_sx : yb) : yf;
+        if (valid) dep_seg(jt, JW, JP, lx, ly, x, y, bx1, by1, s1, qx, qy, qz);
+      }
+      if (__any_sync(0xffffffffu, valid && cut)) {
+        const int c2x = xfirst ? di : 0, c2y = xfirst ? 0 : dj;
+        const R ax2 = xfirst ? xb - R(di) : x_sy;
+        const R ay2 = xfirst ? y_sx : yb - R(dj);
+        const R bx2 = two ? (xfirst ? x_sy - R(di) : xb) : xf;
+        const R by2 = two ? (xfirst ? yb : y_sx - R(dj)) : yf;
+        if (valid && cut)
+          dep_seg(jt, JW, JP, lx + c2x, ly + c2y, ax2, ay2, bx2, by2, s2 - s1,
                   qx, qy, qz);
-        } else if (di == 0) {
-          const R yb = dj > 0 ? R(1) : R(0);
-          const R sy = (yb - y) / (y1 - y);
-          const R xc = x + sy * (x1 - x);
-          dep_seg(js, JW, JP, lx, ly, x, y, xc, yb, sy, qx, qy, qz);
-          dep_seg(js, JW, JP, lx, ly + dj, xc, yb - R(dj), xf, yf, R(1) - sy,
+      }
+      if (__any_sync(0xffffffffu, valid && two)) {
+        const R ax3 = xfirst ? x_sy - R(di) : xb - R(di);
+        const R ay3 = xfirst ? yb - R(dj) : y_sx - R(dj);
+        if (valid && two)
+          dep_seg(jt, JW, JP, lx + di, ly + dj, ax3, ay3, xf, yf, R(1) - s2,
                   qx, qy, qz);
-        } else {
-          const R xb = di > 0 ? R(1) : R(0);
-          const R yb = dj > 0 ? R(1) : R(0);
-          const R sx = (xb - x) / (x1 - x);
-          const R sy = (yb - y) / (y1 - y);
-          const R y_sx = y + sx * (y1 - y);
-          const R x_sy = x + sy * (x1 - x);
-          if (sx <= sy) {
-            dep_seg(js, JW, JP, lx, ly, x, y, xb, y_sx, sx, qx, qy, qz);
-            dep_seg(js, JW, JP, lx + di, ly, xb - R(di), y_sx, x_sy - R(di),
-                    yb, sy - sx, qx, qy, qz);
-            dep_seg(js, JW, JP, lx + di, ly + dj, x_sy - R(di), yb - R(dj), xf,
-                    yf, R(1) - sy, qx, qy, qz);
-          } else {
-            dep_seg(js, JW, JP, lx, ly, x, y, x_sy, yb, sy, qx, qy, qz);
-            dep_seg(js, JW, JP, lx, ly + dj, x_sy, yb - R(dj), xb, y_sx - R(dj),
-                    sx - sy, qx, qy, qz);
-            dep_seg(js, JW, JP, lx + di, ly + dj, xb - R(di), y_sx - R(dj), xf,
-                    yf, R(1) - sx, qx, qy, qz);
-          }
-        }
-
-        // ---- new cell: window shift, boundaries, tile membership ----
-        nix = ix + di - shift;
-        niy = wrap1(iy + dj, S.ny);
-        bool removed = false;
-        if (S.open_x) {
-          removed = nix < 0 || nix >= S.nx;
-        } else {
-          nix = wrap1(nix, S.nx);
-        }
-        if (removed) {
-          ++n_removed;
-        } else if (nix >= x0 && nix < x0 + tw && niy >= y0 && niy < y0 + th) {
-          stay = true;
-        } else {
-          leave = true;
-        }
       }
 
-      // ---- stable compaction of stayers, outbox for leavers ----
+      // ---- new cell: window shift, boundaries, tile membership ----
+      int nix = ix + di - shift;
+      const int niy = wrap1(iy + dj, ny);
+      bool stay = false, leave = false;
+      if (valid) {
+        bool removed = false;
+        if (open_x)
+          removed = nix < 0 || nix >= nx;
+        else
+          nix = wrap1(nix, nx);
+        if (removed)
+          ++n_removed;
+        else if (nix >= x0 && nix < x0 + tw && niy >= y0 && niy < y0 + th)
+          stay = true;
+        else
+          leave = true;
+      }
+
+      // ---- output: stayers to this tile's segment of the other copy,
+      // leavers to the tile's outbox ----
       const unsigned bs = __ballot_sync(0xffffffffu, stay);
       const unsigned bl = __ballot_sync(0xffffffffu, leave);
-      const int buf = chunk & 1;
+      int sb = 0, lb = 0;
       if (lane == 0) {
-        wcnt[buf][warp][0] = __popc(bs);
-        wcnt[buf][warp][1] = __popc(bl);
+        if (bs) sb = atomicAdd(&s_slots[0], __popc(bs));
+        if (bl) lb = atomicAdd(&s_slots[1], __popc(bl));
       }
-      __syncthreads();  // also: every load of this chunk is done
-      int os = 0, ol = 0, ts = 0, tl = 0;
-#pragma unroll
-      for (int q = 0; q < kWarps; ++q) {
-        const int a = wcnt[buf][q][0], b = wcnt[buf][q][1];
-        if (q < warp) {
-          os += a;
-          ol += b;
-        }
-        ts += a;
-        tl += b;
-      }
+      sb = __shfl_sync(0xffffffffu, sb, 0);
+      lb = __shfl_sync(0xffffffffu, lb, 0);
       if (stay) {
-        const size_t d = base + n_stay + os + __popc(bs & lt);
-        P.ix[d] = nix;
-        P.iy[d] = niy;
-        P.x[d] = xf;
-        P.y[d] = yf;
-        P.ux[d] = ux;
-        P.uy[d] = uy;
-        P.uz[d] = uz;
-        if (P.w) P.w[d] = w;
-        if (P.id) P.id[d] = pid;
+        const int d = base + sb + __popc(bs & lt);
+        __stcs(O.ix + d, nix);
+        __stcs(O.iy + d, niy);
+        __stcs(O.x + d, xf);
+        __stcs(O.y + d, yf);
+        __stcs(O.ux + d, ux);
+        __stcs(O.uy + d, uy);
+        __stcs(O.uz + d, uz);
+        if (O.w) __stcs(O.w + d, w);
+        if (O.id) __stcs(O.id + d, pid);
       } else if (leave) {
-        const int slot = n_out + ol + __popc(bl & lt);
-        if (slot < P.ob_cap) {
-          const size_t d = obase + slot;
+        const int slot = lb + __popc(bl & lt);
+        if (slot < ob_cap) {
+          const size_t d = (size_t)tile * ob_cap + slot;
           P.ob_ix[d] = nix;
           P.ob_iy[d] = niy;
           P.ob_x[d] = xf;
@@ -332,8 +405,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           P.ob_ux[d] = ux;
           P.ob_uy[d] = uy;
           P.ob_uz[d] = uz;
-          if (P.w) P.ob_w[d] = w;
-          if (P.id) P.ob_id[d] = pid;
+          if (O.w) P.ob_w[d] = w;
+          if (O.id) P.ob_id[d] = pid;
         } else {
           const int o = atomicAdd(&st->ovf_count, 1);
           if (o < ovf.cap) {
@@ -356,62 +429,68 @@ __global__ void __launch_bounds__(kThreads, 2)
           atomicMin(&st->err_step, step);
         }
       }
-      n_stay += ts;
-      n_out += tl;
-    }
-    if (threadIdx.x == 0) {
-      P.cnt[tile] = n_stay;
-      P.ob_cnt[tile] = min(n_out, P.ob_cap);
     }
     if (n_removed) atomicAdd(&S.removed[s], n_removed);
     if (do_energy)
       block_sum_store<R>((double)kin,
                          &S.part_kin[(size_t)tile * kMaxSpecies + s], red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P.cnt[tile] = s_slots[0];
+      P.ob_cnt[tile] = min(s_slots[1], ob_cap);
+    }
   }
   __syncthreads();
 
   // ---- stage 3b: fold the tile's current (with guards) into global J ----
-  {
-    R *J[3] = {S.J[cur][0], S.J[cur][1], S.J[cur][2]};
-    for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) {
-      const R v = js[k];
-      if (v == R(0)) continue;
-      const int c = k / JP, r = k - c * JP;
-      const int lj = r / JW, li = r - lj * JW;
-      int gi = x0 - 1 + li;
-      const int gj = wrap1(y0 - 1 + lj, S.ny);
-      if (S.open_x) {
-        if (gi < 0 || gi >= S.nx) continue;
-      } else {
-        gi = wrap1(gi, S.nx);
-      }
-      atomicAdd(J[c] + (size_t)gj * S.ld + gi, v);
+  for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) {
+    if (!jt.nonzero(k)) continue;
+    const int c = k / JP, r = k - c * JP;
+    const int lj = r / JW, li = r - lj * JW;
+    int gi = x0 - 1 + li;
+    const int gj = wrap1(y0 - 1 + lj, ny);
+    if (open_x) {
+      if (gi < 0 || gi >= nx) continue;
+    } else {
+      gi = wrap1(gi, nx);
     }
+    atomicAdd(S.J[cur][c] + (size_t)gj * ld + gi, (R)(jt.value(k) * S.jscale[c]));
   }
 }
 
 template <typename R>
 size_t push_smem_bytes(int tx, int ty) {
-  return sizeof(R) * (6 * (size_t)(tx + 2) * (ty + 2) +
-                      3 * (size_t)(tx + 3) * (ty + 3));
+  // 6 field planes of R, then 3 current planes of 8 bytes (two int32 words
+  // in FP32, one double in FP64)
+  return sizeof(R) * 6 * (size_t)(tx + 2) * (ty + 2) +
+         8 * 3 * (size_t)(tx + 3) * (ty + 3);
 }
 
 template <typename R>
 cudaError_t prepare_push_deposit(int max_tx, int max_ty) {
-  return cudaFuncSetAttribute(push_deposit_kernel<R>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)push_smem_bytes<R>(max_tx, max_ty));
+  const int smem = (int)push_smem_bytes<R>(max_tx, max_ty);
+  cudaError_t e = cudaFuncSetAttribute(push_deposit_kernel<R, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(push_deposit_kernel<R, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <typename R>
-cudaError_t launch_push_deposit(const SimDev<R> *sims, const int2 *items,
-                                int n_items, int max_tx, int max_ty,
-                                BatchStatus *st, const OverflowDev<R> &ovf,
+cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
+                                const int2 *items, int n_items, int max_tx,
+                                int max_ty, BatchStatus *st,
+                                const OverflowDev<R> &ovf,
                                 cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
   const size_t smem = push_smem_bytes<R>(max_tx, max_ty);
-  push_deposit_kernel<R><<<n_items, kThreads, smem, stream>>>(sims, items, st,
-                                                              ovf);
+  if (single)
+    push_deposit_kernel<R, false><<<n_items, kThreads, smem, stream>>>(
+        sims, *single, items, st, ovf);
+  else
+    push_deposit_kernel<R, true><<<n_items, kThreads, smem, stream>>>(
+        sims, SimDev<R>{}, items, st, ovf);
   return cudaGetLastError();
 }
 
@@ -420,11 +499,13 @@ template size_t push_smem_bytes<double>(int, int);
 template cudaError_t prepare_push_deposit<float>(int, int);
 template cudaError_t prepare_push_deposit<double>(int, int);
 template cudaError_t launch_push_deposit<float>(const SimDev<float> *,
+                                                const SimDev<float> *,
                                                 const int2 *, int, int, int,
                                                 BatchStatus *,
                                                 const OverflowDev<float> &,
                                                 cudaStream_t);
 template cudaError_t launch_push_deposit<double>(const SimDev<double> *,
+                                                 const SimDev<double> *,
                                                  const int2 *, int, int, int,
                                                  BatchStatus *,
                                                  const OverflowDev<double> &,

@@ -222,8 +222,10 @@ template <typename R>
 struct SpeciesHost {
   zpic_species cfg{};
   bool has_w = false, has_id = false;
+  double q0 = 0.0;       // charge of a weight-1 particle
+  double w_max = 0.0;    // largest weight given through set_particles
   long long total_cap = 0;
-  DevMem ix, iy, id, x, y, ux, uy, uz, w;      // store
+  DevMem store[2];                              // two copies of the store
   DevMem off, cap, cnt, ob_cnt;                 // per tile
   DevMem ob_ix, ob_iy, ob_id, ob_x, ob_y, ob_ux, ob_uy, ob_uz, ob_w;
   int ob_cap = 0;
@@ -423,8 +425,8 @@ class Batch : public BatchBase {
     ZP_TRY(ensure_staging(n + 1));
     ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
                           cudaMemcpyHostToDevice, stream_));
-    ZP_CU(launch_compact<R>(S.dev.sp[s], S.ntiles, (const long long *)stg_off_.p,
-                            stg_, stream_));
+    ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.ntiles,
+                            (const long long *)stg_off_.p, stg_, stream_));
     const bool same = (d->precision == ZPIC_FP64) == (sizeof(R) == 8);
     ZP_CU(cudaMemcpyAsync(d->ix, stg_.ix, 4 * n, cudaMemcpyDeviceToHost, stream_));
     ZP_CU(cudaMemcpyAsync(d->iy, stg_.iy, 4 * n, cudaMemcpyDeviceToHost, stream_));
@@ -489,7 +491,20 @@ class Batch : public BatchBase {
         ZP_CU(cudaStreamSynchronize(stream_));
       }
     }
-    if (src->w) S.sp[s].has_w = true;
+    if (src->w) {
+      S.sp[s].has_w = true;
+      double wm = 0.0;
+      for (long long k = 0; k < n; ++k) {
+        const double v = src->precision == ZPIC_FP64
+                             ? ((const double *)src->w)[k]
+                             : (double)((const float *)src->w)[k];
+        if (!std::isfinite(v) || v < 0)
+          return fail(ZPIC_EINVAL, "weights must be finite and >= 0");
+        wm = std::max(wm, v);
+      }
+      S.sp[s].w_max = std::max(S.sp[s].w_max, wm);
+      set_deposit_units(S);
+    }
     ZP_TRY(rebuild_species(si, s, n, src->w != nullptr, src->id != nullptr,
                            true));
     return ZPIC_OK;
@@ -713,6 +728,7 @@ class Batch : public BatchBase {
       Q.qm = (R)qm;
       Q.hq = (R)(0.5 * qm * S.dt);
       Q.q0 = (R)q0;
+      P.q0 = q0;
       Q.qx = (R)(q0 * S.dx / S.dt);
       Q.qy = (R)(q0 * S.dy / S.dt);
       Q.kin_scale = q0 / qm * S.dx * S.dy;
@@ -727,7 +743,38 @@ class Batch : public BatchBase {
         Q.id_base = (long long)S.nx * S.ny * ppc;
       }
     }
+    set_deposit_units(S);
     return ZPIC_OK;
+  }
+
+  // Deposit factors and the scale of the FP32 fixed-point current tiles:
+  // one unit Uq = max over species of |q0| x (largest weight), so a single
+  // segment adds at most one unit to any current value.
+  void set_deposit_units(SimHost<R> &S) {
+    double uq = 0.0;
+    for (auto &P : S.sp) {
+      double wmax = std::max(1.0, P.w_max);
+      if (P.cfg.profile != ZPIC_PROFILE_NONE) wmax = std::max(wmax, P.cfg.n0);
+      uq = std::max(uq, std::fabs(P.q0) * wmax);
+    }
+    if (!(uq > 0)) uq = 1.0;
+    const double cx = S.dx / S.dt, cy = S.dy / S.dt;
+    const bool fp32 = sizeof(R) == 4;
+    for (int s = 0; s < (int)S.sp.size(); ++s) {
+      SpeciesDev<R> &Q = S.dev.sp[s];
+      const double q0 = S.sp[s].q0;
+      if (fp32) {
+        Q.dq[0] = Q.dq[1] = Q.dq[2] = (R)(q0 / uq * 65536.0);
+      } else {
+        Q.dq[0] = (R)(q0 * cx);
+        Q.dq[1] = (R)(q0 * cy);
+        Q.dq[2] = (R)q0;
+      }
+    }
+    const double u30 = std::ldexp(1.0, -30);
+    S.dev.jscale[0] = fp32 ? uq * cx * u30 : 1.0;
+    S.dev.jscale[1] = fp32 ? uq * cy * u30 : 1.0;
+    S.dev.jscale[2] = fp32 ? uq * u30 : 1.0;
   }
 
   // Allocates the tile store of species s for per-tile counts cnt.
@@ -746,17 +793,15 @@ class Batch : public BatchBase {
       cap[t] = (int)c;
       tot += c;
     }
-    // free previous store
-    for (DevMem *m : {&P.ix, &P.iy, &P.id, &P.x, &P.y, &P.ux, &P.uy, &P.uz, &P.w})
-      dfree(*m);
+    // free the previous store; each copy is one block of planes
+    dfree(P.store[0]);
+    dfree(P.store[1]);
     P.total_cap = tot;
-    if (!dalloc(P.ix, 4 * tot) || !dalloc(P.iy, 4 * tot) ||
-        !dalloc(P.x, sizeof(R) * tot) || !dalloc(P.y, sizeof(R) * tot) ||
-        !dalloc(P.ux, sizeof(R) * tot) || !dalloc(P.uy, sizeof(R) * tot) ||
-        !dalloc(P.uz, sizeof(R) * tot))
-      return fail(ZPIC_ENOMEM, "particle store");
-    if (P.has_w && !dalloc(P.w, sizeof(R) * tot)) return fail(ZPIC_ENOMEM, "w");
-    if (P.has_id && !dalloc(P.id, 4 * tot)) return fail(ZPIC_ENOMEM, "id");
+    const size_t ib = ((size_t)4 * tot + 255) & ~size_t(255);
+    const size_t rb = (sizeof(R) * (size_t)tot + 255) & ~size_t(255);
+    const size_t block = ib * (2 + (P.has_id ? 1 : 0)) + rb * (5 + (P.has_w ? 1 : 0));
+    for (int b = 0; b < 2; ++b)
+      if (!dalloc(P.store[b], block)) return fail(ZPIC_ENOMEM, "particle store");
     if (!P.off.p) {
       if (!dalloc(P.off, 4 * S.ntiles) || !dalloc(P.cap, 4 * S.ntiles) ||
           !dalloc(P.cnt, 4 * S.ntiles) || !dalloc(P.ob_cnt, 4 * S.ntiles))
@@ -781,15 +826,24 @@ class Batch : public BatchBase {
                           cudaMemcpyHostToDevice, stream_));
     ZP_CU(cudaStreamSynchronize(stream_));  // host vectors go out of scope
     SpeciesDev<R> &Q = S.dev.sp[s];
-    Q.ix = (int *)P.ix.p;
-    Q.iy = (int *)P.iy.p;
-    Q.id = (int *)P.id.p;
-    Q.x = (R *)P.x.p;
-    Q.y = (R *)P.y.p;
-    Q.ux = (R *)P.ux.p;
-    Q.uy = (R *)P.uy.p;
-    Q.uz = (R *)P.uz.p;
-    Q.w = (R *)P.w.p;
+    for (int b = 0; b < 2; ++b) {
+      char *c = (char *)P.store[b].p;
+      Planes<R> &L = Q.buf[b];
+      L.ix = (int *)c;
+      L.iy = (int *)(c + ib);
+      c += 2 * ib;
+      L.id = nullptr;
+      if (P.has_id) {
+        L.id = (int *)c;
+        c += ib;
+      }
+      R **reals[5] = {&L.x, &L.y, &L.ux, &L.uy, &L.uz};
+      for (int a = 0; a < 5; ++a) {
+        *reals[a] = (R *)c;
+        c += rb;
+      }
+      L.w = P.has_w ? (R *)c : nullptr;
+    }
     Q.off = (int *)P.off.p;
     Q.cap = (int *)P.cap.p;
     Q.cnt = (int *)P.cnt.p;
@@ -848,6 +902,10 @@ class Batch : public BatchBase {
   }
 
   int upload_descriptors() {
+    // the single-simulation push kernel takes the descriptor by value, so a
+    // captured graph holds a copy: capture again after any change
+    ZP_CU(cudaStreamSynchronize(stream_));
+    invalidate_graph();
     if (!sims_dev_.p && !dalloc(sims_dev_, sizeof(SimDev<R>) * n_sims))
       return fail(ZPIC_ENOMEM, "descriptors");
     std::vector<SimDev<R>> h(n_sims);
@@ -923,6 +981,7 @@ class Batch : public BatchBase {
       lp.x1 = p.x1;
       lp.n0 = p.n0;
       profile_columns(p, S.nx, S.dx, &lp.col_lo, &lp.col_hi);
+      lp.buf = 0;  // step 0 reads copy 0
       ZP_CU(launch_init_load<R>(dptr, S.ntiles, lp, stream_));
     }
     if (S.cfg.laser.enabled) {
@@ -995,8 +1054,8 @@ class Batch : public BatchBase {
                        std::max(64, (int)std::ceil(nominal * slack))));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
-    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], has_w ? 1 : 0,
-                                has_id ? 1 : 0, stream_));
+    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1,
+                                has_w ? 1 : 0, has_id ? 1 : 0, stream_));
     P.h_cnt = cnt;
     ZP_TRY(upload_descriptors());
     ZP_TRY(build_items());
@@ -1040,7 +1099,7 @@ class Batch : public BatchBase {
         ZP_TRY(ensure_staging(n + extra + 1));
         ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
                               cudaMemcpyHostToDevice, stream_));
-        ZP_CU(launch_compact<R>(S.dev.sp[s], S.ntiles,
+        ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.ntiles,
                                 (const long long *)stg_off_.p, stg_, stream_));
         ZP_CU(cudaMemsetAsync(bad_.p, 0, 4, stream_));
         ZP_CU(launch_take_overflow<R>(ovf_, n_ovf, si, s, stg_, n,
@@ -1064,7 +1123,8 @@ class Batch : public BatchBase {
   cudaError_t launch_stage(int k) {
     switch (k) {
       case 0:
-        return launch_push_deposit<R>(dsims(), (const int2 *)items_.p, n_items_,
+        return launch_push_deposit<R>(dsims(), n_sims == 1 ? &sims_[0].dev : nullptr,
+                                      (const int2 *)items_.p, n_items_,
                                       max_tx_, max_ty_, dst(), ovf_, stream_);
       case 1:
         return launch_yee<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
@@ -1146,8 +1206,8 @@ class Batch : public BatchBase {
     if (alloc_) {
       for (auto &S : sims_) {
         for (auto &P : S.sp)
-          for (DevMem *m : {&P.ix, &P.iy, &P.id, &P.x, &P.y, &P.ux, &P.uy, &P.uz,
-                            &P.w, &P.off, &P.cap, &P.cnt, &P.ob_cnt, &P.ob_ix,
+          for (DevMem *m : {&P.store[0], &P.store[1], &P.off, &P.cap, &P.cnt,
+                            &P.ob_cnt, &P.ob_ix,
                             &P.ob_iy, &P.ob_id, &P.ob_x, &P.ob_y, &P.ob_ux,
                             &P.ob_uy, &P.ob_uz, &P.ob_w})
             dfree(*m);

@@ -11,7 +11,8 @@
 //           writes copy (step & 1) ^ 1 (ping-pong, no halo races);
 //   particles, per species: SoA arrays ix, iy (int32), x, y, ux, uy, uz
 //           (R), optional w (R) and id (int32), cut into one segment per
-//           tile [off[t], off[t] + cap[t]) of which cnt[t] are live;
+//           tile [off[t], off[t] + cap[t]) of which cnt[t] are live; two
+//           copies (read one, write the other each step);
 //   outbox, per species: ob_cap slots per tile for particles that leave it.
 #pragma once
 
@@ -42,15 +43,26 @@ struct BatchStatus {
   int pad[2];
 };
 
+// One copy of a species' tile store: SoA planes (w, id may be null).
+template <typename R>
+struct Planes {
+  int *ix, *iy, *id;
+  R *x, *y, *ux, *uy, *uz, *w;
+};
+
 template <typename R>
 struct SpeciesDev {
   R qm;          // charge-to-mass ratio
   R hq;          // (q/m) dt / 2 : Boris half-kick factor
   R qx, qy;      // q0 dx/dt, q0 dy/dt : Jx, Jy per unit cell displacement
   R q0;          // charge of a weight-1 particle
+  R dq[3];       // deposit factors of the shared current tile per component:
+                 // FP32: (q0 / Uq) 2^16 (fixed-point units, see SimDev);
+                 // FP64: q0 dx/dt, q0 dy/dt, q0 (physical units)
   double kin_scale;  // (q0 / (q/m)) dx dy : mass x cell area, weight 1
-  int *ix, *iy, *id;               // id may be null
-  R *x, *y, *ux, *uy, *uz, *w;     // w may be null (all weights 1)
+  // two copies of the store with one segment layout: the push of step n
+  // reads buf[n & 1] and writes buf[(n + 1) & 1]
+  Planes<R> buf[2];
   int *off, *cap, *cnt;            // per tile
   int ob_cap;                      // outbox slots per tile
   int *ob_cnt;                     // per tile
@@ -74,6 +86,10 @@ struct SimDev {
   R dt_dx, dt_dy;              // dt/dx, dt/dy (cells per unit velocity)
   double dx_d, dy_d, dt_d;     // double values (window schedule, setup)
   R *E[2][3], *B[2][3], *J[2][3];
+  // FP32 tiles accumulate J exactly in two-word fixed point with 2^-30 units
+  // of Uq dx/dt, Uq dy/dt, Uq (Uq = max |q0| x max weight, so one segment
+  // contributes at most one unit); jscale converts a tile sum to J.
+  double jscale[3];
   double *part_kin;            // [ntiles][kMaxSpecies] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
   zpic_energy_rec *hist;       // energy history

@@ -18,11 +18,14 @@ size_t push_smem_bytes(int tx, int ty);
 template <typename R>
 cudaError_t prepare_push_deposit(int max_tx, int max_ty);
 
-// Stages 1-3 over all (sim, tile) items.
+// Stages 1-3 over all (sim, tile) items.  `single` (host copy of the only
+// descriptor, or null for a batch) selects the one-simulation kernel that
+// takes the descriptor as a kernel parameter.
 template <typename R>
-cudaError_t launch_push_deposit(const SimDev<R> *sims, const int2 *items,
-                                int n_items, int max_tx, int max_ty,
-                                BatchStatus *st, const OverflowDev<R> &ovf,
+cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
+                                const int2 *items, int n_items, int max_tx,
+                                int max_ty, BatchStatus *st,
+                                const OverflowDev<R> &ovf,
                                 cudaStream_t stream);
 
 // Stage 4 (B half, E, B half) over all (sim, yee block) items; writes the
@@ -60,6 +63,7 @@ struct LoadParams {
   int profile;                  // ZPIC_PROFILE_*
   double x0, x1, n0;
   int col_lo, col_hi;           // loaded cell columns [col_lo, col_hi)
+  int buf;                      // store copy written
 };
 template <typename R>
 cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
@@ -82,11 +86,11 @@ cudaError_t launch_bin_count(Staging<R> in, long long n, int nx, int ny,
 // cursor, must be zero); ids default to the index when in.id is null
 template <typename R>
 cudaError_t launch_bin_scatter(Staging<R> in, long long n,
-                               SpeciesDev<R> sp_host_copy, int has_w,
+                               SpeciesDev<R> sp_host_copy, int buf, int has_w,
                                int has_id, cudaStream_t stream);
-// compacts the tile store into a contiguous staging copy at dst_off[t]
+// compacts store copy `buf` into a contiguous staging copy at dst_off[t]
 template <typename R>
-cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int ntiles,
+cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int buf, int ntiles,
                            const long long *dst_off, Staging<R> out,
                            cudaStream_t stream);
 // appends the overflow entries of (sim, species) to staging at *n_io
