@@ -225,6 +225,13 @@ int zpic_set_particles(zpic_sim *sim, int species, const zpic_particles *src);
 int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
                 size_t *n_written);
 
+/* Energies of the current fields (synchronises): *wE = 1/2 sum E^2 dx dy,
+ * *wB = 1/2 sum B^2 dx dy over the nx*ny cells (Sec. 2.2 fields, the same
+ * quantities as zpic_energy_rec).  Per-row partial sums go to scratch
+ * memory the simulation allocated at creation.  The rows are summed in a
+ * fixed order, so repeated calls give identical results. */
+int zpic_field_energy(zpic_sim *sim, double *wE, double *wB);
+
 /* Fills *info (synchronises). */
 int zpic_get_info(zpic_sim *sim, zpic_info *info);
 

@@ -247,6 +247,62 @@ cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
   return cudaGetLastError();
 }
 
+// ---- field energy of the current fields, on demand ------------------------
+//
+// One CTA per grid row: sums E^2 and B^2 of the row (FP32/FP64 squares,
+// FP64 accumulation, fixed reduction order) and writes the two row sums to
+// scratch[2 j], scratch[2 j + 1]; a one-CTA pass adds the rows in order and
+// writes 1/2 sum E^2 dx dy and 1/2 sum B^2 dx dy to scratch[2 ny], [2 ny + 1].
+// Every scratch value is written before it is read, so the scratch needs no
+// clearing between calls.
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    field_energy_rows_kernel(FieldPtrs<R> f, int nx, int ld, double *scratch) {
+  __shared__ double red[kWarps];
+  const size_t row = (size_t)blockIdx.x * ld;
+  double e = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const R ex = f.e[0][row + i], ey = f.e[1][row + i], ez = f.e[2][row + i];
+    const R bx = f.b[0][row + i], by = f.b[1][row + i], bz = f.b[2][row + i];
+    e += (double)(ex * ex + ey * ey + ez * ez);
+    b += (double)(bx * bx + by * by + bz * bz);
+  }
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x] = e;
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x + 1] = b;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    field_energy_final_kernel(double *scratch, int ny, double half_area) {
+  __shared__ double red[kWarps];
+  double e = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+    e += scratch[2 * (size_t)j];
+    b += scratch[2 * (size_t)j + 1];
+  }
+  e = block_sum(e, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) {
+    scratch[2 * (size_t)ny] = half_area * e;
+    scratch[2 * (size_t)ny + 1] = half_area * b;
+  }
+}
+
+template <typename R>
+cudaError_t launch_field_energy(FieldPtrs<R> f, int nx, int ny, int ld,
+                                double dx, double dy, double *scratch,
+                                cudaStream_t stream) {
+  if (nx <= 0 || ny <= 0) return cudaErrorInvalidValue;
+  field_energy_rows_kernel<R><<<ny, kThreads, 0, stream>>>(f, nx, ld, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  field_energy_final_kernel<<<1, kThreads, 0, stream>>>(scratch, ny,
+                                                        0.5 * dx * dy);
+  return cudaGetLastError();
+}
+
 // ---- laser initialisation ------------------------------------------------
 
 // Gaussian pulse, linear polarisation along y, propagating in +x:
@@ -287,7 +343,10 @@ cudaError_t launch_laser(const SimDev<R> *sim_dev, int nx, int ny,
   template cudaError_t launch_end_step<R>(const SimDev<R> *, int,          \
                                           BatchStatus *, cudaStream_t);     \
   template cudaError_t launch_laser<R>(const SimDev<R> *, int, int,        \
-                                       LaserParams, cudaStream_t);
+                                       LaserParams, cudaStream_t);          \
+  template cudaError_t launch_field_energy<R>(FieldPtrs<R>, int, int, int,  \
+                                              double, double, double *,      \
+                                              cudaStream_t);
 ZP_INST(float)
 ZP_INST(double)
 #undef ZP_INST

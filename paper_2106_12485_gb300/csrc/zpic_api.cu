@@ -199,6 +199,7 @@ struct BatchBase {
   virtual int energy(int sim, zpic_energy_rec *dst, size_t cap,
                      size_t *nw) = 0;
   virtual int info(int sim, zpic_info *out) = 0;
+  virtual int field_energy(int sim, double *wE, double *wB) = 0;
   virtual int tile_counts(int sim, int sp, int32_t *dst, size_t cap) = 0;
   virtual int profile_enable(int en) = 0;
   virtual int profile_read(char *names, size_t name_len, double *ms,
@@ -238,7 +239,7 @@ struct SimHost {
   int nx, ny, ld, tx, ty, ntx, nty, ntiles, ybx, yby;
   double dx, dy, dt;
   DevMem fields;           // 18 planes of ny * ld
-  DevMem part_kin, part_fld, hist, small;
+  DevMem part_kin, part_fld, hist, small, energy_rows;
   int hist_cap = 0;
   std::vector<SpeciesHost<R>> sp;
   SimDev<R> dev{};         // host copy of the descriptor
@@ -527,6 +528,28 @@ class Batch : public BatchBase {
     return ZPIC_OK;
   }
 
+  int field_energy(int si, double *wE, double *wB) override {
+    if (!wE || !wB) return fail(ZPIC_EINVAL, "NULL output");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    const int cur = h_st_->step & 1;
+    FieldPtrs<R> f;
+    for (int c = 0; c < 3; ++c) {
+      f.e[c] = S.dev.E[cur][c];
+      f.b[c] = S.dev.B[cur][c];
+    }
+    double *scratch = (double *)S.energy_rows.p;
+    ZP_CU(launch_field_energy<R>(f, S.nx, S.ny, S.ld, S.dx, S.dy, scratch,
+                                 stream_));
+    double out[2];
+    ZP_CU(cudaMemcpyAsync(out, scratch + 2 * (size_t)S.ny, sizeof(out),
+                          cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    *wE = out[0];
+    *wB = out[1];
+    return ZPIC_OK;
+  }
+
   int info(int si, zpic_info *o) override {
     if (!o) return fail(ZPIC_EINVAL, "NULL info");
     ZP_TRY(sync());
@@ -687,6 +710,8 @@ class Batch : public BatchBase {
       return fail(ZPIC_ENOMEM, "history");
     D.hist = (zpic_energy_rec *)S.hist.p;
     D.hist_cap = S.hist_cap;
+    if (!dalloc(S.energy_rows, sizeof(double) * (2 * (size_t)S.ny + 2)))
+      return fail(ZPIC_ENOMEM, "energy scratch");
     if (!dalloc(S.small, sizeof(int) * (2 + kMaxSpecies)))
       return fail(ZPIC_ENOMEM, "counters");
     ZP_CU(cudaMemsetAsync(S.small.p, 0, S.small.bytes, stream_));
@@ -1211,7 +1236,8 @@ class Batch : public BatchBase {
                             &P.ob_iy, &P.ob_id, &P.ob_x, &P.ob_y, &P.ob_ux,
                             &P.ob_uy, &P.ob_uz, &P.ob_w})
             dfree(*m);
-        for (DevMem *m : {&S.fields, &S.part_kin, &S.part_fld, &S.hist, &S.small})
+        for (DevMem *m : {&S.fields, &S.part_kin, &S.part_fld, &S.hist, &S.small,
+                          &S.energy_rows})
           dfree(*m);
       }
       for (DevMem *m : {&st_mem_, &sims_dev_, &items_, &yee_items_, &ov_sim_,
@@ -1355,6 +1381,11 @@ int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
                 size_t *n_written) {
   ZP_SIM(sim);
   return B->energy(I, dst, cap, n_written);
+}
+
+int zpic_field_energy(zpic_sim *sim, double *wE, double *wB) {
+  ZP_SIM(sim);
+  return B->field_energy(I, wE, wB);
 }
 
 int zpic_get_info(zpic_sim *sim, zpic_info *info) {

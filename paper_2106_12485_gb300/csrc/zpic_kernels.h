@@ -46,6 +46,19 @@ template <typename R>
 cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
                             BatchStatus *st, cudaStream_t stream);
 
+// Device pointers of the six field components (row length ld).
+template <typename R>
+struct FieldPtrs {
+  const R *e[3], *b[3];
+};
+// Field energies 1/2 sum E^2 dx dy, 1/2 sum B^2 dx dy of nx*ny cells.
+// scratch: 2*ny + 2 doubles of device memory; the results are left in
+// scratch[2*ny] (electric) and scratch[2*ny + 1] (magnetic).
+template <typename R>
+cudaError_t launch_field_energy(FieldPtrs<R> f, int nx, int ny, int ld,
+                                double dx, double dy, double *scratch,
+                                cudaStream_t stream);
+
 // Laser fields (Sec. 4.1) added to the current E, B copy of one sim.
 struct LaserParams {
   double E0, omega0, w0, fwhm, x0, yc;

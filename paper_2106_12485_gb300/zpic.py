@@ -95,6 +95,8 @@ _PROTOS = {
     "zpic_set_particles": (C.c_int, [_P, C.c_int, C.POINTER(zpic_particles)]),
     "zpic_energy": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "zpic_get_info": (C.c_int, [_P, C.POINTER(zpic_info)]),
+    "zpic_field_energy": (C.c_int, [_P, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     "zpic_get_tile_counts": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
     "zpic_profile_enable": (C.c_int, [_P, C.c_int]),
     "zpic_profile_read": (C.c_int, [_P, _P, C.c_size_t, _P, _P, C.c_int,
@@ -310,6 +312,12 @@ class Sim:
                                 C.byref(n)), "zpic_energy")
         return [(r.step, r.wE, r.wB, list(r.kin[:r.n_species]))
                 for r in recs[:n.value]]
+
+    def field_energy(self):
+        a, b = C.c_double(), C.c_double()
+        check(lib().zpic_field_energy(self.h, C.byref(a), C.byref(b)),
+              "zpic_field_energy")
+        return a.value, b.value
 
     def tile_counts(self, s):
         i = self.info()

@@ -220,3 +220,22 @@ def test_error_paths():
     sim.step(3)
     assert sim.info().step == 3
     assert sim.num_particles(0) == 0
+
+
+def test_field_energy_matches_oracle():
+    nx, ny = 80, 60
+    fields = P.random_fields(nx, ny, seed=21, scale=0.7)
+    fields = {k: v.astype(np.float32).astype(np.float64)
+              for k, v in fields.items()}
+    cfg = Z.config(nx, ny, (nx * 0.1, ny * 0.2), 0.06, [])
+    gpu = Z.Sim(cfg)
+    from oracle import oracle as O
+    orc = O.Sim(nx, ny, 0.1, 0.2, 0.06)
+    for k, v in fields.items():
+        gpu.set_field(k, v)
+        orc.set_field(k, v)
+    wE, wB = gpu.field_energy()
+    oE, oB = orc.field_energy()
+    assert wE == pytest.approx(oE, rel=1e-6)
+    assert wB == pytest.approx(oB, rel=1e-6)
+    assert gpu.field_energy() == (wE, wB)    # fixed summation order
