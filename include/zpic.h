@@ -232,6 +232,31 @@ int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
  * fixed order, so repeated calls give identical results. */
 int zpic_field_energy(zpic_sim *sim, double *wE, double *wB);
 
+/* The same energies as zpic_field_energy, for callers that cannot
+ * allocate device memory when they need them (code running while a stream
+ * is captured into a CUDA graph, real-time loops that must not wait on an
+ * allocator, hosts that give the library a fixed memory budget).  The paper
+ * has no counterpart; this entry point allocates nothing.
+ *   ex .. bz: device arrays (FP32) of ny rows of ld >= nx values, owned by
+ *             the caller; nx*ny cells of size dx*dy are summed.
+ *   out:      host array of 2 doubles: 1/2 sum E^2 dx dy, 1/2 sum B^2 dx dy.
+ *   stream:   cudaStream_t to run on (NULL: the default stream); the call
+ *             returns after the stream has finished the work.
+ * Scratch: a static device array built into the library for at most 65536
+ * rows (1 MiB + 16 bytes, held by every GPU that loads the library until
+ * exit); ny > 65536 returns ZPIC_EINVAL.  The first call on each device looks
+ * up that array's address with the device current, so make the first call
+ * on a device before capturing any stream.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or several host
+ * threads) race and may return wrong sums.  Nothing in it needs clearing:
+ * each call writes every value it reads.  Errors: ZPIC_EINVAL (NULL pointer,
+ * bad sizes), ZPIC_ECUDA (no device, launch or copy failure). */
+int zpic_field_energy_noalloc_f32(const float *ex, const float *ey,
+                                  const float *ez, const float *bx,
+                                  const float *by, const float *bz, int nx,
+                                  int ny, int ld, double dx, double dy,
+                                  double *out, void *stream);
+
 /* Fills *info (synchronises). */
 int zpic_get_info(zpic_sim *sim, zpic_info *info);
 

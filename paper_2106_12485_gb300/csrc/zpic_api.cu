@@ -38,6 +38,11 @@ static int fail(int code, const std::string &msg) {
   g_last_error = msg;
   return code;
 }
+namespace zp {
+// error reporting for the ABI entry points defined in other files
+int set_last_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace zp
+
 static int cuda_fail(cudaError_t e, const char *what) {
   return fail(ZPIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }

@@ -97,6 +97,8 @@ _PROTOS = {
     "zpic_get_info": (C.c_int, [_P, C.POINTER(zpic_info)]),
     "zpic_field_energy": (C.c_int, [_P, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
+    "zpic_field_energy_noalloc_f32": (C.c_int, [_P] * 6 + [
+        C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P]),
     "zpic_get_tile_counts": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
     "zpic_profile_enable": (C.c_int, [_P, C.c_int]),
     "zpic_profile_read": (C.c_int, [_P, _P, C.c_size_t, _P, _P, C.c_int,
