@@ -192,9 +192,10 @@ def measured_traffic(precision, n_particles, n_cells):
 
 
 def algorithmic_bytes(n_particles, n_cells, real_bytes):
-    # one read + one write of the SoA record (int32 ix, iy + 5 reals) per
-    # particle, plus E, B read and J written once per cell
-    rec = 8 + 5 * real_bytes
+    # one read + one write of the SoA record (16-bit cell within the tile +
+    # x, y, ux, uy, uz) per particle, plus E, B read and J written once per
+    # cell
+    rec = 2 + 5 * real_bytes
     return 2 * rec * n_particles + (6 + 3) * real_bytes * n_cells
 
 

@@ -129,8 +129,7 @@ __global__ void __launch_bounds__(kThreads)
         const int id = O.id ? P.ob_id[e] : 0;
         if (d < cap) {
           const size_t t = base + d;
-          O.ix[t] = ix;
-          O.iy[t] = iy;
+          O.cell[t] = local_cell(ix - x0, iy - y0);
           O.x[t] = P.ob_x[e];
           O.y[t] = P.ob_y[e];
           O.ux[t] = P.ob_ux[e];
@@ -169,8 +168,7 @@ __global__ void __launch_bounds__(kThreads)
           const int d = n_stay + wb + __popc(bal & lt);
           if (d < cap) {
             const size_t t = base + d;
-            O.ix[t] = i;
-            O.iy[t] = j;
+            O.cell[t] = local_cell(i - x0, j - y0);
             O.x[t] = x;
             O.y[t] = y;
             O.ux[t] = R(0);
@@ -262,8 +260,7 @@ __global__ void __launch_bounds__(kThreads)
       w = xc < lp.x0 + lp.x1 ? lp.n0 * (xc - lp.x0) / lp.x1 : lp.n0;
     }
     const size_t t = base + q;
-    O.ix[t] = ix;
-    O.iy[t] = iy;
+    O.cell[t] = local_cell(ix - x0, iy - y0);
     O.x[t] = (R)x;
     O.y[t] = (R)y;
     O.ux[t] = (R)u[0];
@@ -320,7 +317,8 @@ cudaError_t launch_bin_count(Staging<R> in, long long n, int nx, int ny,
 
 template <typename R>
 __global__ void bin_scatter_kernel(Staging<R> in, long long n, SpeciesDev<R> P,
-                                   int b, int has_w, int has_id) {
+                                   int b, int tx, int ty, int has_w,
+                                   int has_id) {
   const Planes<R> &O = P.buf[b];
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -328,8 +326,7 @@ __global__ void bin_scatter_kernel(Staging<R> in, long long n, SpeciesDev<R> P,
     if (t < 0) continue;
     const int slot = atomicAdd(&P.cnt[t], 1);
     const size_t d = (size_t)P.off[t] + slot;
-    O.ix[d] = in.ix[p];
-    O.iy[d] = in.iy[p];
+    O.cell[d] = local_cell(in.ix[p] % tx, in.iy[p] % ty);
     O.x[d] = in.x[p];
     O.y[d] = in.y[p];
     O.ux[d] = in.ux[p];
@@ -342,14 +339,14 @@ __global__ void bin_scatter_kernel(Staging<R> in, long long n, SpeciesDev<R> P,
 
 template <typename R>
 cudaError_t launch_bin_scatter(Staging<R> in, long long n, SpeciesDev<R> sp,
-                               int b, int has_w, int has_id,
+                               int b, int tx, int ty, int has_w, int has_id,
                                cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   const int grid = (int)((n + kThreads - 1) / kThreads < 152 * 16
                              ? (n + kThreads - 1) / kThreads
                              : 152 * 16);
-  bin_scatter_kernel<R><<<grid, kThreads, 0, stream>>>(in, n, sp, b, has_w,
-                                                       has_id);
+  bin_scatter_kernel<R><<<grid, kThreads, 0, stream>>>(in, n, sp, b, tx, ty,
+                                                       has_w, has_id);
   return cudaGetLastError();
 }
 
@@ -357,16 +354,18 @@ cudaError_t launch_bin_scatter(Staging<R> in, long long n, SpeciesDev<R> sp,
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    compact_kernel(SpeciesDev<R> P, int b, const long long *dst_off,
-                   Staging<R> out) {
+    compact_kernel(SpeciesDev<R> P, int b, int tx, int ty, int ntx,
+                   const long long *dst_off, Staging<R> out) {
   const Planes<R> &I = P.buf[b];
   const int t = blockIdx.x;
+  const int x0 = (t % ntx) * tx, y0 = (t / ntx) * ty;
   const int n = P.cnt[t];
   const size_t src = (size_t)P.off[t];
   const size_t dst = (size_t)dst_off[t];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    out.ix[dst + k] = I.ix[src + k];
-    out.iy[dst + k] = I.iy[src + k];
+    const int c = I.cell[src + k];
+    out.ix[dst + k] = x0 + (c & 255);
+    out.iy[dst + k] = y0 + (c >> 8);
     out.x[dst + k] = I.x[src + k];
     out.y[dst + k] = I.y[src + k];
     out.ux[dst + k] = I.ux[src + k];
@@ -378,11 +377,12 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename R>
-cudaError_t launch_compact(SpeciesDev<R> sp, int b, int ntiles,
-                           const long long *dst_off, Staging<R> out,
-                           cudaStream_t stream) {
+cudaError_t launch_compact(SpeciesDev<R> sp, int b, int tx, int ty, int ntx,
+                           int ntiles, const long long *dst_off,
+                           Staging<R> out, cudaStream_t stream) {
   if (ntiles == 0) return cudaSuccess;
-  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, b, dst_off, out);
+  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, b, tx, ty, ntx,
+                                                     dst_off, out);
   return cudaGetLastError();
 }
 
@@ -430,9 +430,9 @@ cudaError_t launch_take_overflow(OverflowDev<R> ovf, int n_entries, int sim,
                                            cudaStream_t);                     \
   template cudaError_t launch_bin_scatter<R>(Staging<R>, long long,           \
                                              SpeciesDev<R>, int, int, int,    \
-                                             cudaStream_t);                   \
-  template cudaError_t launch_compact<R>(SpeciesDev<R>, int, int,             \
-                                         const long long *, Staging<R>,       \
+                                             int, int, cudaStream_t);         \
+  template cudaError_t launch_compact<R>(SpeciesDev<R>, int, int, int, int,   \
+                                         int, const long long *, Staging<R>,  \
                                          cudaStream_t);                       \
   template cudaError_t launch_take_overflow<R>(OverflowDev<R>, int, int, int, \
                                                Staging<R>, long long, int *,  \

@@ -19,7 +19,8 @@
 //     boundary are dropped;
 //  4. adds the shared J tile (interior and guard cells) to the global J
 //     with one reduction per cell (periodic images folded here).
-// Traffic per particle: one read and one write of its SoA record.
+// Traffic per particle: one read and one write of its SoA record (16-bit
+// cell within the tile + 5 reals: 22 bytes in FP32).
 #include "zpic_dev.cuh"
 #include "zpic_kernels.h"
 
@@ -32,54 +33,59 @@ __device__ __forceinline__ float rsqrt_r<float>(float v) { return rsqrtf(v); }
 template <>
 __device__ __forceinline__ double rsqrt_r<double>(double v) { return rsqrt(v); }
 
-// Crossing decision on one axis (identical rule to the method's reading:
-// cross iff o1 >= 1 or o1 < 0; a backward crossing whose new offset rounds
-// to exactly 1 stays in the cell at offset 0).  of = stored offset,
-// oe = path end in the start cell's frame.
 template <typename R>
-__device__ __forceinline__ int axis_cross(R o1, R &of, R &oe) {
-  if (o1 >= R(1)) {
-    of = o1 - R(1);
-    oe = o1;
-    return 1;
-  }
-  if (o1 < R(0)) {
-    const R t = o1 + R(1);
-    if (t == R(1)) {
-      of = R(0);
-      oe = R(0);
-      return 0;
-    }
-    of = t;
-    oe = o1;
-    return -1;
-  }
-  of = o1;
-  oe = o1;
-  return 0;
+__device__ __forceinline__ R fdiv(R a, R b);
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <>
+__device__ __forceinline__ double fdiv<double>(double a, double b) {
+  return a / b;
+}
+
+// Crossing decision on one axis: cross iff o1 >= 1 or o1 < 0; a backward
+// crossing whose new offset rounds to exactly 1 stays in the cell at offset
+// 0.  Returns the cell step; of = stored offset; o1 becomes the path end in
+// the start cell's frame (0 after that rounding fix).  Written with selects
+// only, so lanes never diverge here.
+template <typename R>
+__device__ __forceinline__ int axis_cross(R &o1, R &of) {
+  const bool fwd = o1 >= R(1), back = o1 < R(0);
+  const R t = o1 + R(1);
+  const bool fix = back && t == R(1);
+  of = fwd ? o1 - R(1) : (back ? (fix ? R(0) : t) : o1);
+  o1 = fix ? R(0) : o1;
+  return fwd ? 1 : ((back && !fix) ? -1 : 0);
 }
 
 // Shared current tile.  FP32: each value is an exact fixed-point sum held
-// in two 32-bit words, hi = sum floor(t) and lo = sum round(frac(t) 2^14),
-// for contributions t = c 2^16 with |c| <= 1 unit (value = hi 2^14 + lo in
-// units of 2^-30).  Integer shared atomics are native (float ones are not),
-// and integer sums do not depend on the order of the adds.  The split is
-// exact as long as one word receives fewer than 2^18 adds per step and the
-// net sum stays below 2^15 units.  FP64: plain double atomics.
+// in two int32 words: a contribution t = c 2^16 (|c| <= 1 unit) is split
+// into hi = round(t) and lo = round((t - hi) 2^14) in [-2^13, 2^13], so the
+// value is hi 2^14 + lo in units of 2^-30.  The rounding uses the float
+// "add 1.5 2^23" trick (exact for |t| < 2^22) instead of conversion
+// instructions.  Integer shared atomics are native (float ones are not) and
+// integer sums do not depend on the order of the adds.  Exact while one word
+// receives fewer than 2^18 adds per step and the net sum stays below 2^15
+// units.  FP64: plain double atomics.
 template <typename R>
 struct TileJ;
 
 template <>
 struct TileJ<float> {
   int *hi;
-  unsigned *lo;
+  int *lo;
   __device__ __forceinline__ void add(int idx, float t) const {
-    const float fh = floorf(t);
-    atomicAdd(hi + idx, (int)fh);
-    atomicAdd(lo + idx, (unsigned)__float2int_rn((t - fh) * 16384.0f));
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    const float th = t + M;
+    const int h = __float_as_int(th) - 0x4B400000;
+    const float rem = t - (th - M);
+    const int l = __float_as_int(fmaf(rem, 16384.0f, M)) - 0x4B400000;
+    atomicAdd(hi + idx, h);
+    atomicAdd(lo + idx, l);
   }
   __device__ __forceinline__ bool nonzero(int idx) const {
-    return (hi[idx] | (int)lo[idx]) != 0;
+    return (hi[idx] | lo[idx]) != 0;
   }
   __device__ __forceinline__ double value(int idx) const {
     return (double)hi[idx] * 16384.0 + (double)lo[idx];
@@ -87,7 +93,7 @@ struct TileJ<float> {
   __device__ __forceinline__ void zero(int n) const {
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       hi[k] = 0;
-      lo[k] = 0u;
+      lo[k] = 0;
     }
   }
 };
@@ -105,10 +111,10 @@ struct TileJ<double> {
   }
 };
 
-// One straight segment inside cell (ci, cj) (tile-local), from (xa, ya) to
-// (xb, yb) in that cell's offsets, covering fraction f of the step; qx, qy,
-// qz are the particle's deposit factors.  Planes of JP values, row length
-// JW, origin at cell (-1, -1).
+// One straight segment inside tile cell (ci, cj), from (xa, ya) to (xb, yb)
+// in that cell's offsets, covering fraction f of the step; qx, qy, qz are
+// the particle's deposit factors.  Three planes of JP values, rows of JW,
+// origin at cell (-1, -1).
 template <typename R>
 __device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
                                         int ci, int cj, R xa, R ya, R xb, R yb,
@@ -118,17 +124,19 @@ __device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
   const int b = (cj + 1) * JW + (ci + 1);
   const R ax = qx * ddx, ay = qy * ddy, az = qz * f;
   const R c = ddx * ddy * R(1.0 / 12.0);
+  const R axy = ax * ym, ayx = ay * xm;
   // charge flux through the x faces (i+1/2, j), (i+1/2, j+1)
-  J.add(b, ax * (R(1) - ym));
-  J.add(b + JW, ax * ym);
+  J.add(b, ax - axy);
+  J.add(b + JW, axy);
   // through the y faces (i, j+1/2), (i+1, j+1/2)
-  J.add(JP + b, ay * (R(1) - xm));
-  J.add(JP + b + 1, ay * xm);
+  J.add(JP + b, ay - ayx);
+  J.add(JP + b + 1, ayx);
   // q vz times the path-averaged bilinear weights of the four nodes
-  J.add(2 * JP + b, az * ((R(1) - xm) * (R(1) - ym) + c));
-  J.add(2 * JP + b + 1, az * (xm * (R(1) - ym) - c));
-  J.add(2 * JP + b + JW, az * ((R(1) - xm) * ym - c));
-  J.add(2 * JP + b + JW + 1, az * (xm * ym + c));
+  const R w11 = xm * ym + c, w10 = xm - w11, w01 = ym - w11;
+  J.add(2 * JP + b, az * (R(1) - xm - w01));
+  J.add(2 * JP + b + 1, az * w10);
+  J.add(2 * JP + b + JW, az * w01);
+  J.add(2 * JP + b + JW + 1, az * w11);
 }
 
 template <typename R>
@@ -147,21 +155,11 @@ __device__ __forceinline__ void block_sum_store(double v, double *dst,
   }
 }
 
-template <typename R>
-__device__ __forceinline__ R fdiv(R a, R b);
-template <>
-__device__ __forceinline__ float fdiv<float>(float a, float b) {
-  return __fdividef(a, b);
-}
-template <>
-__device__ __forceinline__ double fdiv<double>(double a, double b) {
-  return a / b;
-}
-
 // kBatch = false: one simulation, its descriptor passed as a grid-constant
-// kernel parameter (fields read from the constant bank, no registers held);
-// kBatch = true: descriptors of many simulations read from device memory.
-template <typename R, bool kBatch>
+// kernel parameter; kBatch = true: descriptors of many simulations read from
+// device memory.  TXC, TYC > 0: tile size fixed at compile time (shared-
+// memory offsets become immediates); 0: taken from the descriptor.
+template <typename R, bool kBatch, int TXC, int TYC>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
     push_deposit_kernel(const SimDev<R> *__restrict__ sims,
                         const __grid_constant__ SimDev<R> one,
@@ -176,7 +174,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
   const int2 it = items[blockIdx.x];
   const SimDev<R> &S = kBatch ? sims[it.x] : one;
   const int tile = it.y;
-  const int nx = S.nx, ny = S.ny, ld = S.ld, TX = S.tx, TY = S.ty;
+  const int nx = S.nx, ny = S.ny, ld = S.ld;
+  const int TX = TXC > 0 ? TXC : S.tx, TY = TYC > 0 ? TYC : S.ty;
   const int open_x = S.open_x, nsp = S.nsp;
   const R dt_dx = S.dt_dx, dt_dy = S.dt_dy;
   const int tcx = tile % S.ntx, tcy = tile / S.ntx;
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
   TileJ<R> jt;
   if constexpr (sizeof(R) == 4) {
     jt.hi = reinterpret_cast<int *>(fs + 6 * FP);
-    jt.lo = reinterpret_cast<unsigned *>(jt.hi + 3 * JP);
+    jt.lo = jt.hi + 3 * JP;
   } else {
     jt.v = reinterpret_cast<double *>(fs + 6 * FP);
   }
@@ -244,12 +243,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       const bool valid = k < n;
       // invalid lanes carry a particle at rest in the tile's first cell and
       // never deposit or store
-      int ix = x0, iy = y0, pid = 0;
+      int lc = 0, pid = 0;
       R x = R(0.5), y = R(0.5), ux = R(0), uy = R(0), uz = R(0), w = R(1);
       if (valid) {
         const int p = base + k;
-        ix = __ldcs(I.ix + p);
-        iy = __ldcs(I.iy + p);
+        lc = __ldcs(I.cell + p);
         x = __ldcs(I.x + p);
         y = __ldcs(I.y + p);
         ux = __ldcs(I.ux + p);
@@ -258,27 +256,26 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
         if (I.w) w = __ldcs(I.w + p);
         if (I.id) pid = __ldcs(I.id + p);
       }
-      int lx = ix - x0, ly = iy - y0;
-      if ((unsigned)lx >= (unsigned)tw || (unsigned)ly >= (unsigned)th) {
+      int lx = lc & 255, ly = lc >> 8;
+      if (lx >= tw || ly >= th) {
         // never produced by the library's own kernels: record it and keep
         // the shared-memory accesses inside the tile
         atomicOr(&st->error, ERR_STORE);
         atomicMin(&st->err_step, step);
-        lx = min(max(lx, 0), tw - 1);
-        ly = min(max(ly, 0), th - 1);
+        lx = min(lx, tw - 1);
+        ly = min(ly, th - 1);
       }
 
       // ---- stage 1: bilinear gather on the staggered grid ----
       // node-centred axis: cell l, weight o; half-staggered axis: cell l-1
       // with weight o+1/2 if o < 1/2, else cell l with weight o-1/2
       const bool xl = x < R(0.5), yl = y < R(0.5);
-      const int hx = xl ? lx - 1 : lx, hy = yl ? ly - 1 : ly;
       const R whx = xl ? x + R(0.5) : x - R(0.5);
       const R why = yl ? y + R(0.5) : y - R(0.5);
       const int b_nn = (ly + 1) * FW + (lx + 1);
-      const int b_hn = (ly + 1) * FW + (hx + 1);
-      const int b_nh = (hy + 1) * FW + (lx + 1);
-      const int b_hh = (hy + 1) * FW + (hx + 1);
+      const int b_hn = b_nn - (xl ? 1 : 0);
+      const int b_nh = b_nn - (yl ? FW : 0);
+      const int b_hh = b_hn - (yl ? FW : 0);
 #define ZP_BILIN(F, b, wx, wy)                                               \
   ((R(1) - (wy)) * ((R(1) - (wx)) * (F)[b] + (wx) * (F)[(b) + 1]) +          \
    (wy) * ((R(1) - (wx)) * (F)[(b) + FW] + (wx) * (F)[(b) + FW + 1]))
@@ -309,8 +306,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       R x1 = x + dt_dx * ux * rgn;
       R y1 = y + dt_dy * uy * rgn;
       R xf, yf;
-      const int di = axis_cross(x1, xf, x1);
-      const int dj = axis_cross(y1, yf, y1);
+      const int di = axis_cross(x1, xf);
+      const int dj = axis_cross(y1, yf);
 
       // ---- stage 3: charge-conserving deposit ----
       // The straight path from (x, y) to (x1, y1) (start-cell frame) is cut
@@ -329,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       const R s1 = xfirst ? sx : sy, s2 = xfirst ? sy : sx;
       const R y_sx = y + sx * (y1 - y);  // where the path meets the x face
       const R x_sy = x + sy * (x1 - x);  // where it meets the y face
-      const bool cut = di != 0 || dj != 0;
+      const bool cut = (di | dj) != 0;
       const bool two = di != 0 && dj != 0;
       {
         const R bx1 = cut ? (xfirst ? xb : x_sy) : xf;
@@ -355,25 +352,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       }
 
       // ---- new cell: window shift, boundaries, tile membership ----
-      int nix = ix + di - shift;
-      const int niy = wrap1(iy + dj, ny);
-      bool stay = false, leave = false;
-      if (valid) {
-        bool removed = false;
-        if (open_x)
-          removed = nix < 0 || nix >= nx;
-        else
-          nix = wrap1(nix, nx);
-        if (removed)
-          ++n_removed;
-        else if (nix >= x0 && nix < x0 + tw && niy >= y0 && niy < y0 + th)
-          stay = true;
-        else
-          leave = true;
-      }
+      int nix = x0 + lx + di - shift;
+      const int niy = wrap1(y0 + ly + dj, ny);
+      bool removed = false;
+      if (open_x)
+        removed = nix < 0 || nix >= nx;
+      else
+        nix = wrap1(nix, nx);
+      const int nlx = nix - x0, nly = niy - y0;
+      const bool inside = (unsigned)nlx < (unsigned)tw && (unsigned)nly < (unsigned)th;
+      const bool stay = valid && !removed && inside;
+      const bool leave = valid && !removed && !inside;
+      if (valid && removed) ++n_removed;
 
       // ---- output: stayers to this tile's segment of the other copy,
-      // leavers to the tile's outbox ----
+      // leavers (global cell) to the tile's outbox ----
       const unsigned bs = __ballot_sync(0xffffffffu, stay);
       const unsigned bl = __ballot_sync(0xffffffffu, leave);
       int sb = 0, lb = 0;
@@ -385,8 +378,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       lb = __shfl_sync(0xffffffffu, lb, 0);
       if (stay) {
         const int d = base + sb + __popc(bs & lt);
-        __stcs(O.ix + d, nix);
-        __stcs(O.iy + d, niy);
+        __stcs(O.cell + d, local_cell(nlx, nly));
         __stcs(O.x + d, xf);
         __stcs(O.y + d, yf);
         __stcs(O.ux + d, ux);
@@ -466,31 +458,50 @@ size_t push_smem_bytes(int tx, int ty) {
          8 * 3 * (size_t)(tx + 3) * (ty + 3);
 }
 
-template <typename R>
-cudaError_t prepare_push_deposit(int max_tx, int max_ty) {
-  const int smem = (int)push_smem_bytes<R>(max_tx, max_ty);
-  cudaError_t e = cudaFuncSetAttribute(push_deposit_kernel<R, false>,
+template <typename R, bool kBatch>
+static cudaError_t set_push_smem(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(push_deposit_kernel<R, kBatch, 16, 16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(push_deposit_kernel<R, true>,
+  return cudaFuncSetAttribute(push_deposit_kernel<R, kBatch, 0, 0>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <typename R>
+cudaError_t prepare_push_deposit(int max_tx, int max_ty) {
+  const int smem = (int)push_smem_bytes<R>(max_tx, max_ty);
+  cudaError_t e = set_push_smem<R, false>(smem);
+  if (e != cudaSuccess) return e;
+  return set_push_smem<R, true>(smem);
 }
 
 template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
-                                int max_ty, BatchStatus *st,
+                                int max_ty, bool all16, BatchStatus *st,
                                 const OverflowDev<R> &ovf,
                                 cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
   const size_t smem = push_smem_bytes<R>(max_tx, max_ty);
-  if (single)
-    push_deposit_kernel<R, false><<<n_items, kThreads, smem, stream>>>(
-        sims, *single, items, st, ovf);
-  else
-    push_deposit_kernel<R, true><<<n_items, kThreads, smem, stream>>>(
-        sims, SimDev<R>{}, items, st, ovf);
+  // the 16 x 16 kernel needs every simulation of the batch to use 16 x 16
+  // tiles (ragged edge tiles are fine)
+  const bool t16 = all16;
+  if (single) {
+    if (t16)
+      push_deposit_kernel<R, false, 16, 16><<<n_items, kThreads, smem, stream>>>(
+          sims, *single, items, st, ovf);
+    else
+      push_deposit_kernel<R, false, 0, 0><<<n_items, kThreads, smem, stream>>>(
+          sims, *single, items, st, ovf);
+  } else {
+    if (t16)
+      push_deposit_kernel<R, true, 16, 16><<<n_items, kThreads, smem, stream>>>(
+          sims, SimDev<R>{}, items, st, ovf);
+    else
+      push_deposit_kernel<R, true, 0, 0><<<n_items, kThreads, smem, stream>>>(
+          sims, SimDev<R>{}, items, st, ovf);
+  }
   return cudaGetLastError();
 }
 
@@ -501,13 +512,13 @@ template cudaError_t prepare_push_deposit<double>(int, int);
 template cudaError_t launch_push_deposit<float>(const SimDev<float> *,
                                                 const SimDev<float> *,
                                                 const int2 *, int, int, int,
-                                                BatchStatus *,
+                                                bool, BatchStatus *,
                                                 const OverflowDev<float> &,
                                                 cudaStream_t);
 template cudaError_t launch_push_deposit<double>(const SimDev<double> *,
                                                  const SimDev<double> *,
                                                  const int2 *, int, int, int,
-                                                 BatchStatus *,
+                                                 bool, BatchStatus *,
                                                  const OverflowDev<double> &,
                                                  cudaStream_t);
 

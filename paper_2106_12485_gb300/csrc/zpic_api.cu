@@ -431,8 +431,9 @@ class Batch : public BatchBase {
     ZP_TRY(ensure_staging(n + 1));
     ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
                           cudaMemcpyHostToDevice, stream_));
-    ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.ntiles,
-                            (const long long *)stg_off_.p, stg_, stream_));
+    ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty, S.ntx,
+                            S.ntiles, (const long long *)stg_off_.p, stg_,
+                            stream_));
     const bool same = (d->precision == ZPIC_FP64) == (sizeof(R) == 8);
     ZP_CU(cudaMemcpyAsync(d->ix, stg_.ix, 4 * n, cudaMemcpyDeviceToHost, stream_));
     ZP_CU(cudaMemcpyAsync(d->iy, stg_.iy, 4 * n, cudaMemcpyDeviceToHost, stream_));
@@ -827,9 +828,10 @@ class Batch : public BatchBase {
     dfree(P.store[0]);
     dfree(P.store[1]);
     P.total_cap = tot;
+    const size_t cb = ((size_t)2 * tot + 255) & ~size_t(255);
     const size_t ib = ((size_t)4 * tot + 255) & ~size_t(255);
     const size_t rb = (sizeof(R) * (size_t)tot + 255) & ~size_t(255);
-    const size_t block = ib * (2 + (P.has_id ? 1 : 0)) + rb * (5 + (P.has_w ? 1 : 0));
+    const size_t block = cb + (P.has_id ? ib : 0) + rb * (5 + (P.has_w ? 1 : 0));
     for (int b = 0; b < 2; ++b)
       if (!dalloc(P.store[b], block)) return fail(ZPIC_ENOMEM, "particle store");
     if (!P.off.p) {
@@ -859,9 +861,8 @@ class Batch : public BatchBase {
     for (int b = 0; b < 2; ++b) {
       char *c = (char *)P.store[b].p;
       Planes<R> &L = Q.buf[b];
-      L.ix = (int *)c;
-      L.iy = (int *)(c + ib);
-      c += 2 * ib;
+      L.cell = (uint16_t *)c;
+      c += cb;
       L.id = nullptr;
       if (P.has_id) {
         L.id = (int *)c;
@@ -952,10 +953,12 @@ class Batch : public BatchBase {
     std::vector<std::pair<long long, int2>> load;
     int yee_n = 0;
     max_tx_ = max_ty_ = 2;
+    all16_ = true;
     for (int i = 0; i < n_sims; ++i) {
       SimHost<R> &S = sims_[i];
       max_tx_ = std::max(max_tx_, S.tx);
       max_ty_ = std::max(max_ty_, S.ty);
+      all16_ = all16_ && S.tx == 16 && S.ty == 16;
       for (int t = 0; t < S.ntiles; ++t) {
         long long l = 0;
         for (auto &P : S.sp) l += P.h_cnt.empty() ? 0 : P.h_cnt[t];
@@ -1084,8 +1087,8 @@ class Batch : public BatchBase {
                        std::max(64, (int)std::ceil(nominal * slack))));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
-    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1,
-                                has_w ? 1 : 0, has_id ? 1 : 0, stream_));
+    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1, S.tx,
+                                S.ty, has_w ? 1 : 0, has_id ? 1 : 0, stream_));
     P.h_cnt = cnt;
     ZP_TRY(upload_descriptors());
     ZP_TRY(build_items());
@@ -1129,8 +1132,9 @@ class Batch : public BatchBase {
         ZP_TRY(ensure_staging(n + extra + 1));
         ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
                               cudaMemcpyHostToDevice, stream_));
-        ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.ntiles,
-                                (const long long *)stg_off_.p, stg_, stream_));
+        ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty,
+                                S.ntx, S.ntiles, (const long long *)stg_off_.p,
+                                stg_, stream_));
         ZP_CU(cudaMemsetAsync(bad_.p, 0, 4, stream_));
         ZP_CU(launch_take_overflow<R>(ovf_, n_ovf, si, s, stg_, n,
                                       (int *)bad_.p, stream_));
@@ -1155,7 +1159,8 @@ class Batch : public BatchBase {
       case 0:
         return launch_push_deposit<R>(dsims(), n_sims == 1 ? &sims_[0].dev : nullptr,
                                       (const int2 *)items_.p, n_items_,
-                                      max_tx_, max_ty_, dst(), ovf_, stream_);
+                                      max_tx_, max_ty_, all16_, dst(), ovf_,
+                                      stream_);
       case 1:
         return launch_yee<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
                              dst(), stream_);
@@ -1273,6 +1278,7 @@ class Batch : public BatchBase {
   OverflowDev<R> ovf_{};
   int ovf_cap_ = 0;
   int n_items_ = 0, n_yee_ = 0, max_tx_ = 2, max_ty_ = 2;
+  bool all16_ = false;
   BatchStatus *h_st_ = nullptr;
   long long target_ = 0;
   int sticky_ = ZPIC_OK;

@@ -9,8 +9,8 @@
 //   fields: E[2][3], B[2][3], J[2][3] arrays of ny rows x ld (ld = nx padded
 //           to 128 bytes); copy (step & 1) is current, the Yee kernel
 //           writes copy (step & 1) ^ 1 (ping-pong, no halo races);
-//   particles, per species: SoA arrays ix, iy (int32), x, y, ux, uy, uz
-//           (R), optional w (R) and id (int32), cut into one segment per
+//   particles, per species: SoA arrays cell (uint16, cell within the tile),
+//           x, y, ux, uy, uz (R), optional w (R) and id (int32), one segment per
 //           tile [off[t], off[t] + cap[t]) of which cnt[t] are live; two
 //           copies (read one, write the other each step);
 //   outbox, per species: ob_cap slots per tile for particles that leave it.
@@ -43,12 +43,19 @@ struct BatchStatus {
   int pad[2];
 };
 
-// One copy of a species' tile store: SoA planes (w, id may be null).
+// One copy of a species' tile store: SoA planes (w, id may be null).  The
+// tile of a particle is implied by the segment it sits in, so only its cell
+// within the tile is stored: cell = (ly << 8) | lx (tiles up to 256 x 256).
 template <typename R>
 struct Planes {
-  int *ix, *iy, *id;
+  uint16_t *cell;
+  int *id;
   R *x, *y, *ux, *uy, *uz, *w;
 };
+
+__host__ __device__ __forceinline__ uint16_t local_cell(int lx, int ly) {
+  return (uint16_t)((ly << 8) | lx);
+}
 
 template <typename R>
 struct SpeciesDev {

@@ -24,7 +24,7 @@ cudaError_t prepare_push_deposit(int max_tx, int max_ty);
 template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
-                                int max_ty, BatchStatus *st,
+                                int max_ty, bool all16, BatchStatus *st,
                                 const OverflowDev<R> &ovf,
                                 cudaStream_t stream);
 
@@ -99,11 +99,14 @@ cudaError_t launch_bin_count(Staging<R> in, long long n, int nx, int ny,
 // cursor, must be zero); ids default to the index when in.id is null
 template <typename R>
 cudaError_t launch_bin_scatter(Staging<R> in, long long n,
-                               SpeciesDev<R> sp_host_copy, int buf, int has_w,
-                               int has_id, cudaStream_t stream);
+                               SpeciesDev<R> sp_host_copy, int buf, int tx,
+                               int ty, int has_w, int has_id,
+                               cudaStream_t stream);
 // compacts store copy `buf` into a contiguous staging copy at dst_off[t]
+// (global cells rebuilt from the tile index and the local cell)
 template <typename R>
-cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int buf, int ntiles,
+cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int buf, int tx,
+                           int ty, int ntx, int ntiles,
                            const long long *dst_off, Staging<R> out,
                            cudaStream_t stream);
 // appends the overflow entries of (sim, species) to staging at *n_io
