@@ -312,15 +312,17 @@ def main():
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
+    resorts0 = sim.info().resorts
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     sim.step(args.steps)
+    sim.sync()          # a capacity re-sort, if any, is inside the region
     e1.record(stream)
-    sim.sync()
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
+    resorts_timed = sim.info().resorts - resorts0
     prof = sim.profile_read(reset=True)
     sim.profile_enable(False)
     ms_max = all_max(ms, world)
@@ -400,6 +402,7 @@ def main():
                          "algorithmic_bytes_per_launch": alg,
                          "avg_launch_ms": push_avg_s * 1e3},
             "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+            "resorts_in_timed_region": resorts_timed,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
         }

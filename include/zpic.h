@@ -125,7 +125,7 @@ typedef struct {
     uint64_t seed;              /* generator seed of the initial load     */
     int sim_index;              /* generator stream of this simulation    */
     int energy_every;           /* record energies every k steps; 0: off  */
-    int tile_x, tile_y;         /* tile size in cells; 0: library default */
+    int tile_x, tile_y;         /* tile size in cells, 2..32; 0: 16       */
     int flags;                  /* ZPIC_TRACK_IDS                         */
     double capacity_slack;      /* spare tile capacity fraction; 0: 0.25  */
 } zpic_config;

@@ -7,11 +7,13 @@
 //  1. stages E, B of the tile plus one guard cell on each side in shared
 //     memory ([-1, tx] x [-1, ty]) and zeroes a shared J tile covering
 //     [-1, tx+1] x [-1, ty+1];
-//  2. streams the tile's particles in chunks of 256 (one per thread):
-//     bilinear gather of the staggered fields from shared memory,
-//     relativistic Boris rotation, move by dt u/gamma (at most one cell,
-//     CFL), split of the straight path at the cell faces it crosses and
-//     accumulation of each segment's current into the shared J tile;
+//  2. streams the tile's particles in chunks of 32 per warp: bilinear
+//     gather of the staggered fields from shared memory, relativistic Boris
+//     rotation, move by dt u/gamma (at most one cell, CFL), split of the
+//     straight path at the cell faces it crosses; the segment in the start
+//     cell goes straight into the shared J tile, the segments of particles
+//     that cross a face wait in a per-warp queue and are deposited 32 at a
+//     time;
 //  3. writes particles that stay in the tile to the tile's segment of the
 //     other copy of the store (each warp claims a run of slots with one
 //     shared-memory atomic, so warps never wait for each other) and
@@ -139,6 +141,46 @@ __device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
   J.add(2 * JP + b + JW + 1, az * w11);
 }
 
+// Per-warp ring of deferred segments: a segment outside the particle's
+// start cell exists only for particles that cross a face (a few percent),
+// but a warp would run the whole deposit whenever any one of its 32 lanes
+// needs it.  Such segments are parked here instead and deposited 32 at a
+// time, one per lane.  SoA, kQ entries: offsets, fraction, deposit factors
+// and the packed tile cell (ci + 1) | (cj + 1) << 8.
+constexpr int kQ = 64;
+
+template <typename R>
+struct SegQueue {
+  R *v;       // 8 planes of kQ values: xa, ya, xb, yb, f, qx, qy, qz
+  int *cell;  // kQ packed cells
+};
+
+template <typename R>
+__device__ __forceinline__ void queue_put(const SegQueue<R> &q, int slot,
+                                          int ci, int cj, R xa, R ya, R xb,
+                                          R yb, R f, R qx, R qy, R qz) {
+  q.v[0 * kQ + slot] = xa;
+  q.v[1 * kQ + slot] = ya;
+  q.v[2 * kQ + slot] = xb;
+  q.v[3 * kQ + slot] = yb;
+  q.v[4 * kQ + slot] = f;
+  q.v[5 * kQ + slot] = qx;
+  q.v[6 * kQ + slot] = qy;
+  q.v[7 * kQ + slot] = qz;
+  q.cell[slot] = (ci + 1) | ((cj + 1) << 8);
+}
+
+template <typename R>
+__device__ __forceinline__ void queue_take(const SegQueue<R> &q,
+                                           const TileJ<R> &J, int JW, int JP,
+                                           int slot) {
+  const int pc = q.cell[slot];
+  dep_seg(J, JW, JP, (pc & 255) - 1, (pc >> 8) - 1, q.v[0 * kQ + slot],
+          q.v[1 * kQ + slot], q.v[2 * kQ + slot], q.v[3 * kQ + slot],
+          q.v[4 * kQ + slot], q.v[5 * kQ + slot], q.v[6 * kQ + slot],
+          q.v[7 * kQ + slot]);
+}
+
 template <typename R>
 __device__ __forceinline__ void block_sum_store(double v, double *dst,
                                                 double *red) {
@@ -194,6 +236,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
   } else {
     jt.v = reinterpret_cast<double *>(fs + 6 * FP);
   }
+  SegQueue<R> q;
+  {
+    // queues after the current planes (8 bytes per value), 16-byte aligned
+    const size_t qoff =
+        ((sizeof(R) * 6 * FP + 8 * 3 * (size_t)JP) + 15) & ~size_t(15);
+    unsigned char *qb = smem_raw + qoff;
+    const int wq = threadIdx.x >> 5;
+    q.v = reinterpret_cast<R *>(qb) + wq * 8 * kQ;
+    q.cell = reinterpret_cast<int *>(qb + sizeof(R) * 8 * kQ * kWarps) +
+             wq * kQ;
+  }
 
   for (int k = threadIdx.x; k < 6 * FP; k += blockDim.x) {
     const int c = k / FP, r = k - c * FP;
@@ -235,6 +288,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
     }
     __syncthreads();  // also: fields staged, J tile zeroed
     int n_removed = 0;
+    int qhead = 0, qtail = 0;  // warp-uniform ring indices
     R kin = R(0);
     // warps work independently on chunks of 32 particles: no block barrier
     // inside the loop; each warp claims its output slots with one atomic
@@ -333,22 +387,44 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
         const R by1 = cut ? (xfirst ? y_sx : yb) : yf;
         if (valid) dep_seg(jt, JW, JP, lx, ly, x, y, bx1, by1, s1, qx, qy, qz);
       }
-      if (__any_sync(0xffffffffu, valid && cut)) {
-        const int c2x = xfirst ? di : 0, c2y = xfirst ? 0 : dj;
-        const R ax2 = xfirst ? xb - R(di) : x_sy;
-        const R ay2 = xfirst ? y_sx : yb - R(dj);
-        const R bx2 = two ? (xfirst ? x_sy - R(di) : xb) : xf;
-        const R by2 = two ? (xfirst ? yb : y_sx - R(dj)) : yf;
-        if (valid && cut)
-          dep_seg(jt, JW, JP, lx + c2x, ly + c2y, ax2, ay2, bx2, by2, s2 - s1,
-                  qx, qy, qz);
-      }
-      if (__any_sync(0xffffffffu, valid && two)) {
-        const R ax3 = xfirst ? x_sy - R(di) : xb - R(di);
-        const R ay3 = xfirst ? yb - R(dj) : y_sx - R(dj);
-        if (valid && two)
-          dep_seg(jt, JW, JP, lx + di, ly + dj, ax3, ay3, xf, yf, R(1) - s2,
-                  qx, qy, qz);
+      // segments outside the start cell wait in the warp's queue
+      const bool need2 = valid && cut, need3 = valid && two;
+      const unsigned m2 = __ballot_sync(0xffffffffu, need2);
+      if (m2) {
+        if (need2) {
+          const int c2x = xfirst ? di : 0, c2y = xfirst ? 0 : dj;
+          const R ax2 = xfirst ? xb - R(di) : x_sy;
+          const R ay2 = xfirst ? y_sx : yb - R(dj);
+          const R bx2 = two ? (xfirst ? x_sy - R(di) : xb) : xf;
+          const R by2 = two ? (xfirst ? yb : y_sx - R(dj)) : yf;
+          queue_put(q, (qtail + __popc(m2 & lt)) & (kQ - 1), lx + c2x,
+                    ly + c2y, ax2, ay2, bx2, by2, s2 - s1, qx, qy, qz);
+        }
+        qtail += __popc(m2);
+        // the ring holds kQ = 64: before each put at most 31 entries wait,
+        // a put adds at most 32, and a full run of 32 is drained at once
+        __syncwarp();
+        if (qtail - qhead >= 32) {
+          queue_take(q, jt, JW, JP, (qhead + lane) & (kQ - 1));
+          qhead += 32;
+          __syncwarp();
+        }
+        const unsigned m3 = __ballot_sync(0xffffffffu, need3);
+        if (m3) {
+          if (need3) {
+            const R ax3 = xfirst ? x_sy - R(di) : xb - R(di);
+            const R ay3 = xfirst ? yb - R(dj) : y_sx - R(dj);
+            queue_put(q, (qtail + __popc(m3 & lt)) & (kQ - 1), lx + di,
+                      ly + dj, ax3, ay3, xf, yf, R(1) - s2, qx, qy, qz);
+          }
+          qtail += __popc(m3);
+          __syncwarp();
+          if (qtail - qhead >= 32) {
+            queue_take(q, jt, JW, JP, (qhead + lane) & (kQ - 1));
+            qhead += 32;
+            __syncwarp();
+          }
+        }
       }
 
       // ---- new cell: window shift, boundaries, tile membership ----
@@ -422,6 +498,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
         }
       }
     }
+    // segments still waiting in the warp's queue
+    __syncwarp();
+    if (lane < qtail - qhead)
+      queue_take(q, jt, JW, JP, (qhead + lane) & (kQ - 1));
     if (n_removed) atomicAdd(&S.removed[s], n_removed);
     if (do_energy)
       block_sum_store<R>((double)kin,
@@ -453,9 +533,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
 template <typename R>
 size_t push_smem_bytes(int tx, int ty) {
   // 6 field planes of R, then 3 current planes of 8 bytes (two int32 words
-  // in FP32, one double in FP64)
-  return sizeof(R) * 6 * (size_t)(tx + 2) * (ty + 2) +
-         8 * 3 * (size_t)(tx + 3) * (ty + 3);
+  // in FP32, one double in FP64), then (16-byte aligned) per warp a queue of
+  // kQ segments of 8 R + 1 int
+  const size_t head = sizeof(R) * 6 * (size_t)(tx + 2) * (ty + 2) +
+                      8 * 3 * (size_t)(tx + 3) * (ty + 3);
+  return ((head + 15) & ~size_t(15)) +
+         (size_t)kWarps * kQ * (8 * sizeof(R) + sizeof(int));
 }
 
 template <typename R, bool kBatch>

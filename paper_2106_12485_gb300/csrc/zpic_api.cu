@@ -120,8 +120,8 @@ int validate(const zpic_config *c) {
     return fail(ZPIC_EINVAL, "n_species out of range");
   if (c->energy_every < 0) return fail(ZPIC_EINVAL, "energy_every < 0");
   if (c->tile_x < 0 || c->tile_y < 0 || c->tile_x == 1 || c->tile_y == 1 ||
-      c->tile_x > 64 || c->tile_y > 64)
-    return fail(ZPIC_EINVAL, "tile sizes must be 0 or in [2, 64]");
+      c->tile_x > 32 || c->tile_y > 32)
+    return fail(ZPIC_EINVAL, "tile sizes must be 0 or in [2, 32]");
   if (c->capacity_slack < 0 || c->capacity_slack > 16)
     return fail(ZPIC_EINVAL, "capacity_slack out of range");
   const double dx = c->box_x / c->nx, dy = c->box_y / c->ny;
