@@ -215,6 +215,13 @@ int zpic_num_particles(zpic_sim *sim, int species, int64_t *n);
 int zpic_get_particles(zpic_sim *sim, int species, const zpic_particles *dst,
                        size_t *n_written);
 
+/* Like zpic_get_particles for the tiles tile_begin <= t < tile_end only
+ * (tile t = ty * ntiles_x + tx of zpic_info), in tile order; for reading a
+ * region of a large simulation without copying all of it. */
+int zpic_get_particles_tiles(zpic_sim *sim, int species, int tile_begin,
+                             int tile_end, const zpic_particles *dst,
+                             size_t *n_written);
+
 /* Replaces the particles of a species with src (copied to the device and
  * sorted into tiles there).  Particles must have 0 <= ix < nx,
  * 0 <= iy < ny and offsets in [0, 1) (ZPIC_EINVAL otherwise). */

@@ -354,14 +354,14 @@ cudaError_t launch_bin_scatter(Staging<R> in, long long n, SpeciesDev<R> sp,
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    compact_kernel(SpeciesDev<R> P, int b, int tx, int ty, int ntx,
+    compact_kernel(SpeciesDev<R> P, int b, int tx, int ty, int ntx, int tile0,
                    const long long *dst_off, Staging<R> out) {
   const Planes<R> &I = P.buf[b];
-  const int t = blockIdx.x;
+  const int t = tile0 + blockIdx.x;
   const int x0 = (t % ntx) * tx, y0 = (t / ntx) * ty;
   const int n = P.cnt[t];
   const size_t src = (size_t)P.off[t];
-  const size_t dst = (size_t)dst_off[t];
+  const size_t dst = (size_t)dst_off[blockIdx.x];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int c = I.cell[src + k];
     out.ix[dst + k] = x0 + (c & 255);
@@ -378,10 +378,10 @@ __global__ void __launch_bounds__(kThreads)
 
 template <typename R>
 cudaError_t launch_compact(SpeciesDev<R> sp, int b, int tx, int ty, int ntx,
-                           int ntiles, const long long *dst_off,
+                           int tile0, int ntiles, const long long *dst_off,
                            Staging<R> out, cudaStream_t stream) {
   if (ntiles == 0) return cudaSuccess;
-  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, b, tx, ty, ntx,
+  compact_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, b, tx, ty, ntx, tile0,
                                                      dst_off, out);
   return cudaGetLastError();
 }
@@ -432,8 +432,8 @@ cudaError_t launch_take_overflow(OverflowDev<R> ovf, int n_entries, int sim,
                                              SpeciesDev<R>, int, int, int,    \
                                              int, int, cudaStream_t);         \
   template cudaError_t launch_compact<R>(SpeciesDev<R>, int, int, int, int,   \
-                                         int, const long long *, Staging<R>,  \
-                                         cudaStream_t);                       \
+                                         int, int, const long long *,         \
+                                         Staging<R>, cudaStream_t);           \
   template cudaError_t launch_take_overflow<R>(OverflowDev<R>, int, int, int, \
                                                Staging<R>, long long, int *,  \
                                                cudaStream_t);

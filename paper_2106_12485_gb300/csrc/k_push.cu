@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       int nix = x0 + lx + di - shift;
       const int niy = wrap1(y0 + ly + dj, ny);
       bool removed = false;
-      if (open_x)
-        removed = nix < 0 || nix >= nx;
+      if (open_x)  // leaves the window it moved in, or the shifted window
+        removed = nix + shift >= nx || nix < 0;
       else
         nix = wrap1(nix, nx);
       const int nlx = nix - x0, nly = niy - y0;

@@ -198,8 +198,8 @@ struct BatchBase {
   virtual int set_fields_f64(int sim, int which, const double *src,
                              size_t n) = 0;
   virtual int num_particles(int sim, int sp, int64_t *n) = 0;
-  virtual int get_particles(int sim, int sp, const zpic_particles *dst,
-                            size_t *nw) = 0;
+  virtual int get_particles(int sim, int sp, int t0, int t1,
+                            const zpic_particles *dst, size_t *nw) = 0;
   virtual int set_particles(int sim, int sp, const zpic_particles *src) = 0;
   virtual int energy(int sim, zpic_energy_rec *dst, size_t cap,
                      size_t *nw) = 0;
@@ -236,6 +236,7 @@ struct SpeciesHost {
   DevMem ob_ix, ob_iy, ob_id, ob_x, ob_y, ob_ux, ob_uy, ob_uz, ob_w;
   int ob_cap = 0;
   std::vector<int> h_cnt;                       // last counts read
+  std::vector<int> h_cap;                       // current tile capacities
 };
 
 template <typename R>
@@ -304,10 +305,18 @@ class Batch : public BatchBase {
   }
 
   int sync() override {
-    for (int attempt = 0; attempt < 16; ++attempt) {
+    // re-sort and re-issue as long as every round advances the step count
+    int stalled = 0, last_step = -1;
+    for (;;) {
       ZP_CU(cudaStreamSynchronize(stream_));
       ZP_TRY(read_status());
       const BatchStatus &st = *h_st_;
+      if (st.step == last_step) {
+        if (++stalled > 3) break;
+      } else {
+        stalled = 0;
+      }
+      last_step = st.step;
       if (st.error & ERR_LOST) {
         sticky_ = fail(ZPIC_EOVERFLOW, "particle storage exhausted");
         return sticky_;
@@ -409,7 +418,7 @@ class Batch : public BatchBase {
     return ZPIC_OK;
   }
 
-  int get_particles(int si, int s, const zpic_particles *d,
+  int get_particles(int si, int s, int t0, int t1, const zpic_particles *d,
                     size_t *nw) override {
     if (!d || !d->ix || !d->iy || !d->x || !d->y || !d->ux || !d->uy || !d->uz)
       return fail(ZPIC_EINVAL, "NULL particle array");
@@ -418,21 +427,24 @@ class Batch : public BatchBase {
     ZP_TRY(sync());
     SimHost<R> &S = sims_[si];
     if (s < 0 || s >= (int)S.sp.size()) return fail(ZPIC_EINVAL, "species");
+    if (t1 < 0) t1 = S.ntiles;
+    if (t0 < 0 || t0 > t1 || t1 > S.ntiles)
+      return fail(ZPIC_EINVAL, "tile range");
     ZP_TRY(read_counts(si, s));
     SpeciesHost<R> &P = S.sp[s];
-    std::vector<long long> off(S.ntiles);
+    std::vector<long long> off(std::max(1, t1 - t0));
     long long n = 0;
-    for (int t = 0; t < S.ntiles; ++t) {
-      off[t] = n;
+    for (int t = t0; t < t1; ++t) {
+      off[t - t0] = n;
       n += P.h_cnt[t];
     }
     if (nw) *nw = (size_t)n;
     if ((size_t)n > d->cap) return fail(ZPIC_ECAP, "particle buffer too small");
     ZP_TRY(ensure_staging(n + 1));
-    ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
+    ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * off.size(),
                           cudaMemcpyHostToDevice, stream_));
     ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty, S.ntx,
-                            S.ntiles, (const long long *)stg_off_.p, stg_,
+                            t0, t1 - t0, (const long long *)stg_off_.p, stg_,
                             stream_));
     const bool same = (d->precision == ZPIC_FP64) == (sizeof(R) == 8);
     ZP_CU(cudaMemcpyAsync(d->ix, stg_.ix, 4 * n, cudaMemcpyDeviceToHost, stream_));
@@ -746,7 +758,11 @@ class Batch : public BatchBase {
         cnt[t] = cb > ca ? (cb - ca) * th * ppc : 0;
       }
       const double nominal = (double)ppc * S.tx * S.ty;
-      const int min_extra = std::max(64, (int)std::ceil(nominal * slack));
+      // room to grow; a species the moving window injects will fill every
+      // tile to its full density, so its tiles start with that room
+      const bool injected = c.moving_window && P.cfg.profile != ZPIC_PROFILE_NONE;
+      const int min_extra = std::max(
+          64, (int)std::ceil(nominal * (injected ? 1.0 + slack : slack)));
       P.ob_cap = ((std::max(64, (int)std::ceil(nominal * (c.moving_window ? 0.25 : 0.125))) + 31) / 32) * 32;
       ZP_TRY(alloc_store(i, s, cnt, slack, min_extra));
       // the initial load writes cnt particles per tile directly
@@ -818,6 +834,10 @@ class Batch : public BatchBase {
     for (int t = 0; t < S.ntiles; ++t) {
       long long c = std::max<long long>((long long)std::ceil(cnt[t] * (1.0 + slack)),
                                         (long long)cnt[t] + min_extra);
+      // a tile that outgrew its capacity at least doubles it, so a tile that
+      // keeps filling (a moving front) needs few re-sorts
+      if (!P.h_cap.empty() && cnt[t] > P.h_cap[t])
+        c = std::max<long long>(c, 2LL * P.h_cap[t]);
       c = (c + 31) / 32 * 32;
       if (tot + c > INT_MAX) return fail(ZPIC_ENOMEM, "species store exceeds 2^31");
       off[t] = (int)tot;
@@ -856,6 +876,7 @@ class Batch : public BatchBase {
                           cudaMemcpyHostToDevice, stream_));
     ZP_CU(cudaMemcpyAsync(P.cap.p, cap.data(), 4 * S.ntiles,
                           cudaMemcpyHostToDevice, stream_));
+    P.h_cap = cap;
     ZP_CU(cudaStreamSynchronize(stream_));  // host vectors go out of scope
     SpeciesDev<R> &Q = S.dev.sp[s];
     for (int b = 0; b < 2; ++b) {
@@ -1083,8 +1104,11 @@ class Batch : public BatchBase {
       return fail(ZPIC_EINVAL, "particles outside the grid or offsets not in [0,1)");
     const double slack = S.cfg.capacity_slack > 0 ? S.cfg.capacity_slack : 0.25;
     const double nominal = (double)P.cfg.ppc_x * P.cfg.ppc_y * S.tx * S.ty;
+    const bool injected =
+        S.cfg.moving_window && P.cfg.profile != ZPIC_PROFILE_NONE;
     ZP_TRY(alloc_store(si, s, cnt, slack,
-                       std::max(64, (int)std::ceil(nominal * slack))));
+                       std::max(64, (int)std::ceil(
+                                        nominal * (injected ? 1.0 + slack : slack)))));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1, S.tx,
@@ -1133,8 +1157,8 @@ class Batch : public BatchBase {
         ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
                               cudaMemcpyHostToDevice, stream_));
         ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty,
-                                S.ntx, S.ntiles, (const long long *)stg_off_.p,
-                                stg_, stream_));
+                                S.ntx, 0, S.ntiles,
+                                (const long long *)stg_off_.p, stg_, stream_));
         ZP_CU(cudaMemsetAsync(bad_.p, 0, 4, stream_));
         ZP_CU(launch_take_overflow<R>(ovf_, n_ovf, si, s, stg_, n,
                                       (int *)bad_.p, stream_));
@@ -1380,7 +1404,15 @@ int zpic_num_particles(zpic_sim *sim, int species, int64_t *n) {
 int zpic_get_particles(zpic_sim *sim, int species, const zpic_particles *dst,
                        size_t *n_written) {
   ZP_SIM(sim);
-  return B->get_particles(I, species, dst, n_written);
+  return B->get_particles(I, species, 0, -1, dst, n_written);
+}
+
+int zpic_get_particles_tiles(zpic_sim *sim, int species, int tile_begin,
+                             int tile_end, const zpic_particles *dst,
+                             size_t *n_written) {
+  ZP_SIM(sim);
+  if (tile_end < 0) return fail(ZPIC_EINVAL, "tile range");
+  return B->get_particles(I, species, tile_begin, tile_end, dst, n_written);
 }
 
 int zpic_set_particles(zpic_sim *sim, int species, const zpic_particles *src) {

@@ -102,11 +102,12 @@ cudaError_t launch_bin_scatter(Staging<R> in, long long n,
                                SpeciesDev<R> sp_host_copy, int buf, int tx,
                                int ty, int has_w, int has_id,
                                cudaStream_t stream);
-// compacts store copy `buf` into a contiguous staging copy at dst_off[t]
-// (global cells rebuilt from the tile index and the local cell)
+// compacts tiles [tile0, tile0 + ntiles) of store copy `buf` into a
+// contiguous staging copy, tile tile0 + k from dst_off[k] on (global cells
+// rebuilt from the tile index and the local cell)
 template <typename R>
 cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int buf, int tx,
-                           int ty, int ntx, int ntiles,
+                           int ty, int ntx, int tile0, int ntiles,
                            const long long *dst_off, Staging<R> out,
                            cudaStream_t stream);
 // appends the overflow entries of (sim, species) to staging at *n_io

@@ -92,6 +92,9 @@ _PROTOS = {
     "zpic_num_particles": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64)]),
     "zpic_get_particles": (C.c_int, [_P, C.c_int, C.POINTER(zpic_particles),
                                      C.POINTER(C.c_size_t)]),
+    "zpic_get_particles_tiles": (C.c_int, [_P, C.c_int, C.c_int, C.c_int,
+                                           C.POINTER(zpic_particles),
+                                           C.POINTER(C.c_size_t)]),
     "zpic_set_particles": (C.c_int, [_P, C.c_int, C.POINTER(zpic_particles)]),
     "zpic_energy": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "zpic_get_info": (C.c_int, [_P, C.POINTER(zpic_info)]),
@@ -263,11 +266,16 @@ class Sim:
               "zpic_num_particles")
         return n.value
 
-    def particles(self, s, dtype=None, with_w=True, with_id=True, out=None):
-        """Particles of species s as a dict of numpy arrays (tile order)."""
+    def particles(self, s, dtype=None, with_w=True, with_id=True, out=None,
+                  tiles=None):
+        """Particles of species s as a dict of numpy arrays (tile order);
+        tiles = (begin, end) restricts the copy to those tiles."""
         if dtype is None:
             dtype = np.float64 if self.info().precision == FP64 else np.float32
-        n = self.num_particles(s)
+        if tiles is not None:
+            n = int(self.tile_counts(s)[tiles[0]:tiles[1]].sum())
+        else:
+            n = self.num_particles(s)
         if out is None:
             out = {k: np.empty(n, np.int32) for k in ("ix", "iy")}
             for k in ("x", "y", "ux", "uy", "uz"):
@@ -282,8 +290,13 @@ class Sim:
         for k in ("ix", "iy", "x", "y", "ux", "uy", "uz", "w", "id"):
             setattr(p, k, _ptr(out.get(k)))
         nw = C.c_size_t()
-        check(lib().zpic_get_particles(self.h, s, C.byref(p), C.byref(nw)),
-              "zpic_get_particles")
+        if tiles is not None:
+            check(lib().zpic_get_particles_tiles(self.h, s, tiles[0], tiles[1],
+                                                 C.byref(p), C.byref(nw)),
+                  "zpic_get_particles_tiles")
+        else:
+            check(lib().zpic_get_particles(self.h, s, C.byref(p), C.byref(nw)),
+                  "zpic_get_particles")
         m = nw.value
         return {k: v[:m] for k, v in out.items()}
 

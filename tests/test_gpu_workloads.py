@@ -1,0 +1,184 @@
+"""GPU parity on the benchmark workloads (through the C ABI), against the
+FP64 oracle on the same seeded inputs:
+
+* laser-wakefield shape: Gaussian laser, moving window, cold plasma
+  injected through the window behind a density ramp;
+* batched simulations (one launch per stage for all of them) against the
+  oracle and against the same simulations created one by one;
+* the full-size uniform plasma (2048^2 cells, 536,870,912 particles): one
+  step, checked on a sampled region the oracle recomputes from the
+  regenerated initial load, plus exact particle counts;
+* the precision study: FP32 and FP64 forms against the oracle at step 20.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_12485_gb300 import workloads as W
+from paper_2106_12485_gb300 import zpic as Z
+from synthetic import plasma as P
+from tests import pichelpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_from_load(cfg, loads, window=None, cap_extra=0):
+    species = []
+    for s, ld in enumerate(loads):
+        sp = cfg.species[s]
+        species.append(H.oracle_species(ld, sp.q_over_m, sp.ppc_x * sp.ppc_y,
+                                        cap=len(ld["ix"]) + cap_extra))
+    dx, dy = cfg.box_x / cfg.nx, cfg.box_y / cfg.ny
+    return O.Sim(cfg.nx, cfg.ny, dx, dy, cfg.dt, open_x=bool(cfg.bc_x),
+                 species=species, window=window)
+
+
+def empty_load():
+    z = np.zeros(0)
+    return {"ix": np.zeros(0, np.int32), "iy": np.zeros(0, np.int32),
+            "x": z, "y": z, "ux": z, "uy": z, "uz": z, "w": z,
+            "id": np.zeros(0, np.int32)}
+
+
+def test_lwfa_window_laser_injection_parity():
+    # 400 steps: the plasma entering through the window reaches the laser
+    # (about 300 cells behind the right edge) and carries real currents;
+    # before that its displacements are below the FP32 offset resolution
+    nx, ny, steps = 512, 32, 400
+    cfg = W.lwfa(nx=nx, ny=ny, track_ids=True, energy_every=10)
+    Lx = nx * 0.02
+    gpu = Z.Sim(cfg)
+    window = {"species": [{"ppc_x": 2, "ppc_y": 2, "ramp_x0": Lx,
+                           "ramp_len": 5.0, "n0": 1.0,
+                           "id_base": nx * ny * 4}]}
+    orc = oracle_from_load(cfg, [empty_load()], window=window,
+                           cap_extra=steps * ny * 4 + 16)
+    l = cfg.laser
+    orc.laser(l.a0, l.omega0, l.w0, l.fwhm, l.x0, l.y_center)
+    H.compare_fields(gpu, orc, 1e-6, names=H.FIELDS[:6])   # laser init
+    gpu.step(steps)
+    orc.step(steps)
+    assert gpu.info().n_shift == orc.n_shift > 350
+    assert gpu.num_particles(0) == orc.species[0].n > 0
+    H.compare_fields(gpu, orc, 1e-4)
+    H.compare_particles(gpu, orc, 0, nx, ny, 1e-4)
+    # energy records agree (laser field energy dominates)
+    for (st, wE, wB, kin), (ost, owE, owB, okin) in zip(gpu.energy(),
+                                                         orc.history[9::10]):
+        assert st == ost
+        assert wE == pytest.approx(owE, rel=1e-4)
+        assert wB == pytest.approx(owB, rel=1e-4)
+        assert kin[0] == pytest.approx(okin[0], rel=1e-3, abs=1e-9 * owE)
+
+
+def batch_configs():
+    return [
+        W.uniform_thermal(48, 40, ppc=(2, 2), sim_index=0, track_ids=True),
+        W.clouds(64, 32, ppc=(2, 2), sim_index=1, track_ids=True),
+        W.uniform_thermal(32, 32, ppc=(3, 3), u_th=0.2, sim_index=2,
+                          track_ids=True),
+        W.uniform_thermal(40, 24, ppc=(2, 2), sim_index=3, track_ids=True,
+                          energy_every=5),
+    ]
+
+
+def test_batch_matches_oracle_and_single_sims():
+    cfgs = batch_configs()
+    batch = Z.Batch(cfgs)
+    singles = [Z.Sim(c) for c in cfgs]
+    batch.step(10)
+    for s in singles:
+        s.step(10)
+    for i, c in enumerate(cfgs):
+        view = batch.sim(i)
+        for name in H.FIELDS:
+            a, b = view.field(name), singles[i].field(name)
+            assert H.rel_l2(a, b) <= 1e-5, (i, name)
+        for sp in range(c.n_species):
+            g = H.by_id(view.particles(sp))
+            r = H.by_id(singles[i].particles(sp))
+            np.testing.assert_array_equal(g["id"], r["id"])
+            np.testing.assert_allclose(g["ux"], r["ux"], rtol=0, atol=1e-5)
+    # sim 0 against the oracle on the regenerated load
+    ld = P.plasma_load(48, 40, 2, 2, sim=0, u_th=(0.1, 0.1, 0.1))
+    orc = oracle_from_load(cfgs[0], [ld])
+    x0 = H.positions_by_id(orc.species[0].state())
+    orc.step(10)
+    H.compare_fields(batch.sim(0), orc, 1e-4)
+    H.compare_particles(batch.sim(0), orc, 0, 48, 40, 1e-4, x_ref=x0)
+    assert len(batch.sim(3).energy()) == 2
+
+
+def test_full_size_uniform_plasma_sampled_parity():
+    nx = ny = 2048
+    cfg = W.precision_study(track_ids=True)
+    gpu = Z.Sim(cfg)
+    n_each = nx * ny * 64
+    assert gpu.num_particles(0) == n_each and gpu.num_particles(1) == n_each
+    gpu.step(1)
+    assert gpu.num_particles(0) == n_each and gpu.num_particles(1) == n_each
+    info = gpu.info()
+    # region: tiles (64..65, 64..65) = cells [1024, 1056)^2; the oracle gets
+    # the initial load of cells [1020, 1060)^2 (margin of 4 cells)
+    T = info.tile_x
+    t_lo = 1024 // T
+    lo, hi = 1020, 1060
+    cx, cy = np.meshgrid(np.arange(lo, hi), np.arange(lo, hi))
+    cells = (cy * nx + cx).ravel()
+    loads = []
+    for s in range(2):
+        ld = P.plasma_load(nx, ny, 8, 8, species=s, u_th=(0.1, 0.1, 0.1),
+                           cells=cells)
+        ld["ix"] = ld["ix"] - lo
+        ld["iy"] = ld["iy"] - lo
+        loads.append(ld)
+    sub = W.precision_study(hi - lo, hi - lo)
+    orc = oracle_from_load(sub, loads)
+    orc.step(1)
+    for s in range(2):
+        got = []
+        for ty in (t_lo, t_lo + 1):
+            t0 = ty * info.ntiles_x + t_lo
+            got.append(gpu.particles(s, tiles=(t0, t0 + 2)))
+        g = H.by_id({k: np.concatenate([d[k] for d in got]) for k in got[0]})
+        o = H.by_id(orc.species[s].state())
+        keep = np.isin(o["id"], g["id"])
+        o = {k: v[keep] for k, v in o.items()}
+        np.testing.assert_array_equal(g["id"], o["id"])
+        # global positions (a particle ending within rounding of a face may
+        # sit on either side of it in FP32 and FP64)
+        for c, f in (("ix", "x"), ("iy", "y")):
+            np.testing.assert_allclose(g[c] + g[f].astype(np.float64),
+                                       o[c] + lo + o[f], rtol=0, atol=2e-6)
+        for k in ("ux", "uy", "uz"):
+            np.testing.assert_allclose(g[k], o[k], rtol=0, atol=2e-6)
+    # fields in the interior of the region (4+ cells from the oracle edge)
+    a, b = 1024 - lo, 1056 - lo
+    for name in H.FIELDS:
+        gf = gpu.field(name)[1024:1056, 1024:1056]
+        of = orc.f[name][a:b, a:b]
+        assert H.rel_l2(gf, of) <= 1e-4, name
+
+
+@pytest.mark.parametrize("nx", [128])
+def test_precision_study_fp32_vs_fp64(nx):
+    errs = {}
+    for prec in (Z.FP32, Z.FP64):
+        dt = np.float64 if prec == Z.FP64 else np.float32
+        cfg = W.precision_study(nx, nx, ppc=(4, 4), precision=prec,
+                                track_ids=True)
+        loads = [P.plasma_load(nx, nx, 4, 4, species=s,
+                               u_th=(0.1, 0.1, 0.1), dtype=dt)
+                 for s in range(2)]
+        gpu = Z.Sim(cfg)
+        orc = oracle_from_load(cfg, loads)
+        refs = [H.positions_by_id(sp.state()) for sp in orc.species]
+        gpu.step(20)
+        orc.step(20)
+        f = max(H.compare_fields(gpu, orc, 1e-4).values())
+        p = max(max(H.compare_particles(gpu, orc, s, nx, nx, 1e-4,
+                                        x_ref=refs[s]).values())
+                for s in range(2))
+        errs[prec] = (f, p)
+    assert errs[Z.FP64][0] < 1e-9 and errs[Z.FP64][1] < 1e-9
+    assert errs[Z.FP64][0] < errs[Z.FP32][0] / 100
