@@ -55,6 +55,11 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512,
                     help="cells per side of the oracle sample")
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "clouds", "lwfa", "batch",
+                             "precision"],
+                    help="uniform (default): the large uniform plasma; the "
+                    "others print one line for that workload")
     return ap.parse_args()
 
 
@@ -276,11 +281,146 @@ def workload_config(args):
 
 # --------------------------------------------------------------- main ----
 
+def timed_steps(sim, stream, steps, torch):
+    """CUDA-event time (ms) of `steps` steps, any re-sort included."""
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    sim.sync()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def base_line(metric_value, ms, args, dtype, config, **extra):
+    out = {"metric": "particle-steps/s", "value": metric_value,
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": dtype, "data": "synthetic", "config": config}
+    out.update(extra)
+    return out
+
+
+def other_workload(args):
+    """Lines for the workloads other than the large uniform plasma."""
+    import torch
+    from paper_2106_12485_gb300 import workloads as W
+    from paper_2106_12485_gb300 import zpic as Z
+    from synthetic import plasma as P
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    if args.workload in ("clouds", "lwfa"):
+        if args.workload == "clouds":
+            cfg = W.clouds(energy_every=10)
+            warm = args.warmup
+            desc = ("collision of plasma clouds 1024x1024, e-/e+ 4x4 ppc in "
+                    "two clouds drifting +-0.2, u_th 0.05, FP32")
+        else:
+            cfg = W.lwfa(energy_every=10)
+            warm = max(args.warmup, 2000)   # let the plasma fill the window
+            desc = ("laser wakefield 4096x512, a0=2 w0=10 laser, moving "
+                    "window, cold e- 2x2 ppc behind a ramp, FP32")
+        sim = Z.Sim(cfg)
+        sim.set_stream(stream.cuda_stream)
+        sim.step(warm)
+        sim.sync()
+        info = sim.info()
+        n0 = sum(info.n_particles[:info.n_species])
+        r0 = info.resorts
+        ms = timed_steps(sim, stream, args.steps, torch)
+        info = sim.info()
+        n1 = sum(info.n_particles[:info.n_species])
+        ps = 0.5 * (n0 + n1) * args.steps
+        print(json.dumps(base_line(
+            ps / (ms / 1e3), ms, args, "f32",
+            {"workload": desc, "nx": cfg.nx, "ny": cfg.ny,
+             "particles_start": int(n0), "particles_end": int(n1),
+             "steps_before_timing": warm},
+            resorts_in_timed_region=info.resorts - r0,
+            step_after=int(info.step))))
+        return
+    if args.workload == "batch":
+        specs = P.batch_specs(256)
+        cfgs = W.batch_sweep(specs)
+        batch = Z.Batch(cfgs)
+        batch.set_stream(stream.cuda_stream)
+        batch.step(args.warmup)
+        batch.sync()
+        n = 0
+        for i in range(len(cfgs)):
+            inf = batch.sim(i).info()
+            n += sum(inf.n_particles[:inf.n_species])
+        ms_b = timed_steps(batch, stream, args.steps, torch)
+        del batch
+        sims = [Z.Sim(c) for c in cfgs]
+        for sm in sims:
+            sm.set_stream(stream.cuda_stream)
+            sm.step(args.warmup)
+        for sm in sims:
+            sm.sync()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for sm in sims:
+                sm.step(1)
+        for sm in sims:
+            sm.sync()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        ps = float(n) * args.steps
+        print(json.dumps(base_line(
+            ps / (ms_b / 1e3), ms_b, args, "f32",
+            {"workload": "batched sweep: 256 independent sims 32-256 cells "
+                         "per side, 4-64 ppc, half thermal, half clouds",
+             "sims": len(cfgs), "particles": int(n)},
+            per_sim_launches={"value": ps / (ms_s / 1e3),
+                              "ms_per_step": ms_s / args.steps},
+            batched_over_per_sim=ms_s / ms_b)))
+        return
+    if args.workload == "precision":
+        res = {}
+        for name, prec in (("fp32", Z.FP32), ("fp64", Z.FP64)):
+            cfg = W.precision_study(args.nx, args.ny, ppc=(args.ppc, args.ppc),
+                                    precision=prec, energy_every=1)
+            sim = Z.Sim(cfg)
+            sim.set_stream(stream.cuda_stream)
+            inf = sim.info()
+            n = sum(inf.n_particles[:2])
+            ms = timed_steps(sim, stream, args.steps, torch)
+            e = sim.energy()
+            tot = [r[1] + r[2] + sum(r[3]) for r in e]
+            drift = max(abs(t - tot[0]) for t in tot) / tot[0]
+            res[name] = {"value": n * args.steps / (ms / 1e3),
+                         "ms_per_step": ms / args.steps,
+                         "energy_drift": drift}
+            del sim
+        print(json.dumps(base_line(
+            res["fp32"]["value"], res["fp32"]["ms_per_step"] * args.steps,
+            args, "f32",
+            {"workload": "precision study, uniform plasma %dx%d, e-/e+ %dx%d "
+                         "ppc, u_th 0.1, dt 0.07" % (args.nx, args.ny,
+                                                    args.ppc, args.ppc)},
+            fp32=res["fp32"], fp64=res["fp64"],
+            fp32_over_fp64=res["fp32"]["value"] / res["fp64"]["value"])))
+        return
+
+
 def main():
     args = parse_args()
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload != "uniform":
+        if rank == 0:
+            other_workload(args)
         return
     import torch
     from paper_2106_12485_gb300 import workloads as W
