@@ -63,53 +63,69 @@ __device__ __forceinline__ int axis_cross(R &o1, R &of) {
 
 // Shared current tile.  FP32: each value is an exact fixed-point sum held
 // in two int32 words: a contribution t = c 2^16 (|c| <= 1 unit) is split
-// into hi = round(t) and lo = round((t - hi) 2^14) in [-2^13, 2^13], so the
-// value is hi 2^14 + lo in units of 2^-30.  The rounding uses the float
-// "add 1.5 2^23" trick (exact for |t| < 2^22) instead of conversion
-// instructions.  Integer shared atomics are native (float ones are not) and
-// integer sums do not depend on the order of the adds.  Exact while one word
-// receives fewer than 2^18 adds per step and the net sum stays below 2^15
-// units.  FP64: plain double atomics.
+// into h = round(t) and l = round((t - h) 2^14) in [-2^13, 2^13], so the
+// value is h 2^14 + l in units of 2^-30.  Both roundings use the float
+// "add 1.5 2^23" trick (exact for |t| < 2^22): the words receive the bit
+// patterns K + h and K + l (K = 0x4B400000) and the bias n K of a word that
+// received n adds is removed when the tile is folded, n coming from a count
+// of segments per base cell.  Integer shared atomics are native (float ones
+// are not) and integer sums do not depend on the order of the adds.  Exact
+// while one word receives fewer than 2^18 adds per step and the net sum
+// stays below 2^15 units.  FP64: plain double atomics.
 template <typename R>
 struct TileJ;
 
 template <>
 struct TileJ<float> {
-  int *hi;
-  int *lo;
+  int *hi;   // 3 planes
+  int *lo;   // 3 planes
+  int *cnt;  // segments per base cell (one plane)
+  static constexpr unsigned kBias = 0x4B400000u;  // bits of 1.5 * 2^23
+  __device__ __forceinline__ void seg(int b) const { atomicAdd(cnt + b, 1); }
   __device__ __forceinline__ void add(int idx, float t) const {
-    const float M = 12582912.0f;  // 1.5 * 2^23
-    const float th = t + M;
-    const int h = __float_as_int(th) - 0x4B400000;
-    const float rem = t - (th - M);
-    const int l = __float_as_int(fmaf(rem, 16384.0f, M)) - 0x4B400000;
-    atomicAdd(hi + idx, h);
-    atomicAdd(lo + idx, l);
+    const float M = 12582912.0f;                // 1.5 * 2^23
+    const float C = 206158430208.0f + M;        // M (1 + 2^14)
+    const float th = t + M;                     // M + h
+    const float tl = fmaf(t, 16384.0f, fmaf(-th, 16384.0f, C));  // M + l
+    atomicAdd(hi + idx, __float_as_int(th));
+    atomicAdd(lo + idx, __float_as_int(tl));
   }
-  __device__ __forceinline__ bool nonzero(int idx) const {
-    return (hi[idx] | lo[idx]) != 0;
+  // value of word idx (plane c, position r in the plane), 2^-30 units;
+  // returns false when it is zero
+  __device__ __forceinline__ bool value(int c, int r, int JW, int JP,
+                                        double &v) const {
+    unsigned n = (unsigned)cnt[r];
+    if (r >= 1 && c != 0) n += (unsigned)cnt[r - 1];
+    if (r >= JW && c != 1) n += (unsigned)cnt[r - JW];
+    if (r >= JW + 1 && c == 2) n += (unsigned)cnt[r - JW - 1];
+    const int h = (int)((unsigned)hi[c * JP + r] - n * kBias);
+    const int l = (int)((unsigned)lo[c * JP + r] - n * kBias);
+    v = (double)h * 16384.0 + (double)l;
+    return (h | l) != 0;
   }
-  __device__ __forceinline__ double value(int idx) const {
-    return (double)hi[idx] * 16384.0 + (double)lo[idx];
-  }
-  __device__ __forceinline__ void zero(int n) const {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  __device__ __forceinline__ void zero(int JP) const {
+    for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) {
       hi[k] = 0;
       lo[k] = 0;
     }
+    for (int k = threadIdx.x; k < JP; k += blockDim.x) cnt[k] = 0;
   }
 };
 
 template <>
 struct TileJ<double> {
   double *v;
+  __device__ __forceinline__ void seg(int) const {}
   __device__ __forceinline__ void add(int idx, double t) const {
     atomicAdd(v + idx, t);
   }
-  __device__ __forceinline__ bool nonzero(int idx) const { return v[idx] != 0.0; }
-  __device__ __forceinline__ double value(int idx) const { return v[idx]; }
-  __device__ __forceinline__ void zero(int n) const {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) v[k] = 0.0;
+  __device__ __forceinline__ bool value(int c, int r, int, int JP,
+                                        double &out) const {
+    out = v[c * JP + r];
+    return out != 0.0;
+  }
+  __device__ __forceinline__ void zero(int JP) const {
+    for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) v[k] = 0.0;
   }
 };
 
@@ -127,6 +143,7 @@ __device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
   const R ax = qx * ddx, ay = qy * ddy, az = qz * f;
   const R c = ddx * ddy * R(1.0 / 12.0);
   const R axy = ax * ym, ayx = ay * xm;
+  J.seg(b);
   // charge flux through the x faces (i+1/2, j), (i+1/2, j+1)
   J.add(b, ax - axy);
   J.add(b + JW, axy);
@@ -141,44 +158,196 @@ __device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
   J.add(2 * JP + b + JW + 1, az * w11);
 }
 
-// Per-warp ring of deferred segments: a segment outside the particle's
-// start cell exists only for particles that cross a face (a few percent),
-// but a warp would run the whole deposit whenever any one of its 32 lanes
-// needs it.  Such segments are parked here instead and deposited 32 at a
-// time, one per lane.  SoA, kQ entries: offsets, fraction, deposit factors
-// and the packed tile cell (ci + 1) | (cj + 1) << 8.
+// The path of a particle in its start cell's frame, from (x, y) to
+// (x1, y1), split at the cell faces it crosses: cross iff the end lies at or
+// beyond a face (axis_cross); sx, sy = path parameters where it meets the x
+// face xb and the y face yb (1 when that axis is not crossed); s1 = min,
+// s2 = max, an exact tie counting as x first.  Segment 1 lies in the start
+// cell, segment 2 in the cell entered at s1, segment 3 (two crossings) in
+// the final cell; each is written in its own cell's frame and the last one
+// ends at the stored offsets (xf, yf).  The same code serves the particle
+// loop and the deferred segments, so both see the same rounding.
+template <typename R>
+struct PathSplit {
+  int di, dj;     // cell steps
+  R xf, yf;       // offsets in the final cell
+  R xb, yb;       // crossed faces in the start cell's frame
+  R sx, sy, s1, s2;
+  R x_sx_y, x_sy;  // y where the path meets the x face, x where it meets y
+  bool xfirst, cut, two;
+};
+
+template <typename R>
+__device__ __forceinline__ PathSplit<R> split_path(R x, R y, R x1, R y1) {
+  PathSplit<R> p;
+  p.di = axis_cross(x1, p.xf);
+  p.dj = axis_cross(y1, p.yf);
+  p.xb = p.di > 0 ? R(1) : R(0);
+  p.yb = p.dj > 0 ? R(1) : R(0);
+  p.sx = p.di ? fdiv<R>(p.xb - x, x1 - x) : R(1);
+  p.sy = p.dj ? fdiv<R>(p.yb - y, y1 - y) : R(1);
+  p.xfirst = p.sx <= p.sy;
+  p.s1 = p.xfirst ? p.sx : p.sy;
+  p.s2 = p.xfirst ? p.sy : p.sx;
+  p.x_sx_y = y + p.sx * (y1 - y);
+  p.x_sy = x + p.sy * (x1 - x);
+  p.cut = (p.di | p.dj) != 0;
+  p.two = p.di != 0 && p.dj != 0;
+  return p;
+}
+
+// Per-warp ring of particles whose path crosses a face: the segment in the
+// start cell is deposited at once, the one or two segments beyond wait here
+// and are deposited 32 particles at a time, one per lane, so that the few
+// lanes that need them (a crossing is a few-percent event) do not hold up
+// the warp.  Entries keep the raw path (start, end as computed, weight,
+// z-deposit factor, start cell) and the split is recomputed when they are
+// taken.  SoA, kQ entries; the ring is drained before the species changes.
 constexpr int kQ = 64;
+constexpr int kQVals = 6;
 
 template <typename R>
 struct SegQueue {
-  R *v;       // 8 planes of kQ values: xa, ya, xb, yb, f, qx, qy, qz
-  int *cell;  // kQ packed cells
+  R *v;       // kQVals planes of kQ values: x, y, x1, y1, w, qz
+  int *cell;  // kQ packed start cells (lx + 1) | (ly + 1) << 8
 };
 
 template <typename R>
 __device__ __forceinline__ void queue_put(const SegQueue<R> &q, int slot,
-                                          int ci, int cj, R xa, R ya, R xb,
-                                          R yb, R f, R qx, R qy, R qz) {
-  q.v[0 * kQ + slot] = xa;
-  q.v[1 * kQ + slot] = ya;
-  q.v[2 * kQ + slot] = xb;
-  q.v[3 * kQ + slot] = yb;
-  q.v[4 * kQ + slot] = f;
-  q.v[5 * kQ + slot] = qx;
-  q.v[6 * kQ + slot] = qy;
-  q.v[7 * kQ + slot] = qz;
-  q.cell[slot] = (ci + 1) | ((cj + 1) << 8);
+                                          int lx, int ly, R x, R y, R x1, R y1,
+                                          R w, R qz) {
+  q.v[0 * kQ + slot] = x;
+  q.v[1 * kQ + slot] = y;
+  q.v[2 * kQ + slot] = x1;
+  q.v[3 * kQ + slot] = y1;
+  q.v[4 * kQ + slot] = w;
+  q.v[5 * kQ + slot] = qz;
+  q.cell[slot] = (lx + 1) | ((ly + 1) << 8);
 }
 
 template <typename R>
 __device__ __forceinline__ void queue_take(const SegQueue<R> &q,
                                            const TileJ<R> &J, int JW, int JP,
-                                           int slot) {
+                                           int slot, R qx0, R qy0) {
   const int pc = q.cell[slot];
-  dep_seg(J, JW, JP, (pc & 255) - 1, (pc >> 8) - 1, q.v[0 * kQ + slot],
-          q.v[1 * kQ + slot], q.v[2 * kQ + slot], q.v[3 * kQ + slot],
-          q.v[4 * kQ + slot], q.v[5 * kQ + slot], q.v[6 * kQ + slot],
-          q.v[7 * kQ + slot]);
+  const int lx = (pc & 255) - 1, ly = (pc >> 8) - 1;
+  const R x = q.v[0 * kQ + slot], y = q.v[1 * kQ + slot];
+  const R w = q.v[4 * kQ + slot], qz = q.v[5 * kQ + slot];
+  const PathSplit<R> p =
+      split_path(x, y, q.v[2 * kQ + slot], q.v[3 * kQ + slot]);
+  const R qx = qx0 * w, qy = qy0 * w;
+  // segment 2: from the first crossing point into the cell entered there
+  const int c2x = p.xfirst ? p.di : 0, c2y = p.xfirst ? 0 : p.dj;
+  const R ax2 = p.xfirst ? p.xb - R(p.di) : p.x_sy;
+  const R ay2 = p.xfirst ? p.x_sx_y : p.yb - R(p.dj);
+  const R bx2 = p.two ? (p.xfirst ? p.x_sy - R(p.di) : p.xb) : p.xf;
+  const R by2 = p.two ? (p.xfirst ? p.yb : p.x_sx_y - R(p.dj)) : p.yf;
+  dep_seg(J, JW, JP, lx + c2x, ly + c2y, ax2, ay2, bx2, by2, p.s2 - p.s1, qx,
+          qy, qz);
+  if (p.two) {
+    // segment 3: from the second crossing point into the final cell
+    const R ax3 = p.xfirst ? p.x_sy - R(p.di) : p.xb - R(p.di);
+    const R ay3 = p.xfirst ? p.yb - R(p.dj) : p.x_sx_y - R(p.dj);
+    dep_seg(J, JW, JP, lx + p.di, ly + p.dj, ax3, ay3, p.xf, p.yf,
+            R(1) - p.s2, qx, qy, qz);
+  }
+}
+
+// Field tile in coefficient form: for every cell (ci, cj) of a component's
+// own (staggered) grid, the bilinear interpolant over that cell written as
+// a + b wx + c wy + d wx wy, so a gather is one 16-byte shared load and
+// three FMAs.  Grid of (TX + 1) x (TY + 1) cells with origin (-1, -1): a
+// half-staggered axis may start one cell left of the particle's cell.
+template <typename R>
+struct alignas(16) Coef4 {
+  R a, b, c, d;
+};
+
+template <typename R>
+__device__ __forceinline__ R interp(const Coef4<R> *F, int idx, R wx, R wy) {
+  const Coef4<R> k = F[idx];
+  return fma(fma(k.d, wx, k.c), wy, fma(k.b, wx, k.a));
+}
+
+// ---- particle-copy ring: asynchronous 16-byte copies global -> shared ----
+// Each warp streams its chunks of 32 particles through kStages stages of its
+// own: while a chunk is computed, the copies of the next kStages - 1 chunks
+// are in flight (cp.async, tracked per thread in commit groups), without
+// holding registers.  A stage holds the chunk's planes back to back: cell
+// (32 x 2 bytes), x, y, ux, uy, uz (32 x 4 bytes each), then w and id when
+// the species stores them, i.e. 44 to 60 pieces of 16 bytes; lane l copies
+// pieces l and l + 32.  FP32 only (FP64 loads directly).
+template <typename R>
+struct Ring {
+  static constexpr int kStages = sizeof(R) == 4 ? 2 : 0;
+  static constexpr unsigned kRB = 32 * sizeof(R);  // one real plane
+  __host__ __device__ static constexpr unsigned stage_bytes(bool w, bool id) {
+    return 64 + 5 * kRB + (w ? kRB : 0) + (id ? 128 : 0);
+  }
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One lane's share of a stage: up to two 16-byte pieces.  For piece q the
+// source is plane(q) + (p0 << shift(q)) + 16 (q - first piece of the plane),
+// p0 being the chunk's first particle (a multiple of 32: segment offsets and
+// capacities are multiples of 32, so all 32 slots lie inside the segment).
+struct RingLane {
+  const char *src[2];
+  unsigned sh[2];
+  unsigned dst[2];  // shared addresses relative to the stage
+  int n;            // pieces of this lane (0..2)
+};
+
+template <typename R>
+__device__ __forceinline__ RingLane ring_lane(const Planes<R> &I, int lane) {
+  RingLane r;
+  const int np = (int)Ring<R>::stage_bytes(I.w != nullptr, I.id != nullptr) / 16;
+  r.n = 0;
+  for (int k = 0; k < 2; ++k) {
+    const int q = lane + 32 * k;
+    r.src[k] = nullptr;
+    r.sh[k] = 0;
+    r.dst[k] = 16u * q;
+    if (q >= np) continue;
+    r.n = k + 1;
+    if (q < 4) {
+      r.src[k] = reinterpret_cast<const char *>(I.cell) + 16 * q;
+      r.sh[k] = 1;
+      continue;
+    }
+    const int pl = (q - 4) >> 3, o = (q - 4) & 7;
+    const void *pp = pl == 0   ? (const void *)I.x
+                     : pl == 1 ? (const void *)I.y
+                     : pl == 2 ? (const void *)I.ux
+                     : pl == 3 ? (const void *)I.uy
+                     : pl == 4 ? (const void *)I.uz
+                     : pl == 5 ? (I.w ? (const void *)I.w : (const void *)I.id)
+                               : (const void *)I.id;
+    r.src[k] = reinterpret_cast<const char *>(pp) + 16 * o;
+    r.sh[k] = 2;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void ring_issue(const RingLane &r, unsigned stg,
+                                           int p0) {
+  if (r.n > 0) cp_async16(stg + r.dst[0], r.src[0] + ((size_t)p0 << r.sh[0]));
+  if (r.n > 1) cp_async16(stg + r.dst[1], r.src[1] + ((size_t)p0 << r.sh[1]));
 }
 
 template <typename R>
@@ -197,61 +366,382 @@ __device__ __forceinline__ void block_sum_store(double v, double *dst,
   }
 }
 
-// kBatch = false: one simulation, its descriptor passed as a grid-constant
-// kernel parameter; kBatch = true: descriptors of many simulations read from
-// device memory.  TXC, TYC > 0: tile size fixed at compile time (shared-
-// memory offsets become immediates); 0: taken from the descriptor.
-template <typename R, bool kBatch, int TXC, int TYC>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
-    push_deposit_kernel(const SimDev<R> *__restrict__ sims,
-                        const __grid_constant__ SimDev<R> one,
-                        const int2 *__restrict__ items, BatchStatus *st,
-                        OverflowDev<R> ovf) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_slots[2];  // stayers written, leavers written
-  __shared__ double red[kWarps];
+// A particle that leaves its tile goes to the tile's outbox (global cell
+// index), or, when the outbox is full, to the overflow buffer that the host
+// drains by re-sorting.  Out of line: few particles take this path, and its
+// pointers would otherwise occupy registers in the particle loop.
+template <typename R>
+__device__ __noinline__ void park_leaver(const SpeciesDev<R> &P,
+                                         const OverflowDev<R> &ovf,
+                                         BatchStatus *st, int tile, int slot,
+                                         int sim, int s, int step, int nix,
+                                         int niy, R xf, R yf, R ux, R uy, R uz,
+                                         R w, int pid, bool has_w,
+                                         bool has_id) {
+  const int ob_cap = P.ob_cap;
+  if (slot < ob_cap) {
+    const size_t d = (size_t)tile * ob_cap + slot;
+    P.ob_ix[d] = nix;
+    P.ob_iy[d] = niy;
+    P.ob_x[d] = xf;
+    P.ob_y[d] = yf;
+    P.ob_ux[d] = ux;
+    P.ob_uy[d] = uy;
+    P.ob_uz[d] = uz;
+    if (has_w) P.ob_w[d] = w;
+    if (has_id) P.ob_id[d] = pid;
+    return;
+  }
+  const int o = atomicAdd(&st->ovf_count, 1);
+  if (o < ovf.cap) {
+    ovf.sim[o] = sim;
+    ovf.species[o] = s;
+    ovf.ix[o] = nix;
+    ovf.iy[o] = niy;
+    ovf.x[o] = xf;
+    ovf.y[o] = yf;
+    ovf.ux[o] = ux;
+    ovf.uy[o] = uy;
+    ovf.uz[o] = uz;
+    ovf.w[o] = w;
+    ovf.id[o] = pid;
+    atomicOr(&st->error, ERR_OVERFLOW);
+  } else {
+    atomicAdd(&st->lost, 1);
+    atomicOr(&st->error, ERR_LOST);
+  }
+  atomicMin(&st->err_step, step);
+}
 
-  const int step = st->step;
-  if (frozen(st, step)) return;
-  const int2 it = items[blockIdx.x];
-  const SimDev<R> &S = kBatch ? sims[it.x] : one;
-  const int tile = it.y;
+// Shared-memory layout of the push kernel for tx x ty tiles (byte offsets):
+// the coefficient tile (6 components x (tx+1)(ty+1) cells), the current
+// tile (3 planes of (tx+3)(ty+3) values, 8 bytes each: two int32 words in
+// FP32, one double in FP64), the FP32 segment counts (one int plane), the
+// per-warp segment queues, which first serve as the staging area of the
+// raw field values (6 planes of (tx+2)(ty+2)), and (FP32) the particle-copy
+// ring: kStages stages per warp.
+template <typename R>
+struct PushSmem {
+  size_t coef, j, cnt, q, ring, stages, total;
+  __host__ __device__ PushSmem(int tx, int ty, bool wide) {
+    const size_t CP = (size_t)(tx + 1) * (ty + 1);
+    const size_t JP = (size_t)(tx + 3) * (ty + 3);
+    coef = 0;
+    j = 6 * CP * sizeof(Coef4<R>);
+    cnt = j + 3 * JP * 8;
+    const size_t cnt_bytes = sizeof(R) == 4 ? JP * sizeof(int) : 0;
+    q = (cnt + cnt_bytes + 15) & ~size_t(15);
+    const size_t qbytes =
+        (size_t)kWarps * kQ * (kQVals * sizeof(R) + sizeof(int));
+    const size_t raw = 6 * (size_t)(tx + 2) * (ty + 2) * sizeof(R);
+    ring = (q + (qbytes > raw ? qbytes : raw) + 15) & ~size_t(15);
+    constexpr int S = Ring<R>::kStages;
+    stages = ring;
+    total = stages + (size_t)kWarps * S * Ring<R>::stage_bytes(wide, wide);
+  }
+};
+
+// State shared by the chunk loops of one CTA.
+template <typename R>
+struct TileCtx {
+  const Coef4<R> *cf;  // coefficient tile, 6 planes of CP cells
+  int CW, CP, JW, JP;
+  TileJ<R> jt;
+  SegQueue<R> q;
+  unsigned char *stages;  // particle-copy ring
+  int x0, y0, tw, th, nx, ny;
+  int tile, sim, step, shift;
+  R dt_dx, dt_dy;
+  bool do_energy;
+  int *s_slots;
+  double *red;
+};
+
+// One species of one tile.  kSpec: the species' layout and the boundary are
+// compile-time facts (kPlain: no weight or id planes; kOpen: open x boundary
+// with a moving window possible); otherwise they are read at run time.
+template <typename R, int CUR, bool kSpec, bool kPlain, bool kOpen>
+__device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
+                                             TileCtx<R> &T, unsigned &g,
+                                             BatchStatus *st,
+                                             const OverflowDev<R> &ovf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const SpeciesDev<R> &P = S.sp[s];
+  const Planes<R> &I = P.buf[CUR];
+  const Planes<R> &O = P.buf[CUR ^ 1];
+  const bool has_w = kSpec ? !kPlain : I.w != nullptr;
+  const bool has_id = kSpec ? !kPlain : I.id != nullptr;
+  const bool open_x = kSpec ? kOpen : S.open_x != 0;
+  const R hq = P.hq, qx0 = P.dq[0], qy0 = P.dq[1], q00 = P.dq[2];
+  const int n = P.cnt[T.tile];
+  const int base = P.off[T.tile];
+  const int tw = T.tw, th = T.th, CW = T.CW, CP = T.CP, JW = T.JW, JP = T.JP;
+  const Coef4<R> *cEx = T.cf, *cEy = T.cf + CP, *cEz = T.cf + 2 * CP;
+  const Coef4<R> *cBx = T.cf + 3 * CP, *cBy = T.cf + 4 * CP,
+                 *cBz = T.cf + 5 * CP;
+  if (threadIdx.x == 0) {
+    T.s_slots[0] = 0;
+    T.s_slots[1] = 0;
+  }
+  __syncthreads();  // also: coefficient tile ready, J tile zeroed
+  int n_removed = 0;
+  int qhead = 0, qtail = 0;  // warp-uniform ring indices
+  R kin = R(0);
+
+  // warps work independently on chunks of 32 particles: no block barrier
+  // inside the loop; each warp claims its output slots with one atomic.
+  // Chunk jc of warp `warp` starts at particle warp * 32 + jc * kThreads.
+  constexpr int kS = Ring<R>::kStages;
+  const int nch = n > warp * 32 ? (n - warp * 32 + kThreads - 1) / kThreads : 0;
+  const unsigned sbytes = Ring<R>::stage_bytes(has_w, has_id);
+  const unsigned stg0 = smem_addr(T.stages) + warp * kS * sbytes;
+  RingLane rl;
+  if constexpr (kS > 0) {
+    rl = ring_lane(I, lane);
+    // prologue: chunks 0 .. kS-2 (one commit group each, empty or not)
+    for (int jc = 0; jc < kS - 1; ++jc) {
+      if (jc < nch)
+        ring_issue(rl, stg0 + ((g + jc) % kS) * sbytes,
+                   base + warp * 32 + jc * kThreads);
+      cp_async_commit();
+    }
+  }
+  for (int jc = 0; jc < nch; ++jc, ++g) {
+    const int c0 = warp * 32 + jc * kThreads;
+    // lanes past the end repeat the last particle with zero weight: they
+    // run the same instructions, deposit nothing and store nothing
+    const bool valid = c0 + lane < n;
+    const int kk = valid ? lane : n - 1 - c0;  // slot within the chunk
+    int lc;
+    R x, y, ux, uy, uz, w = R(1);
+    int pid = 0;
+    if constexpr (kS > 0) {
+      // the stage of chunk jc + kS - 1 was read in the previous iteration
+      __syncwarp();
+      if (jc + kS - 1 < nch)
+        ring_issue(rl, stg0 + ((g + kS - 1) % kS) * sbytes,
+                   c0 + base + (kS - 1) * kThreads);
+      cp_async_commit();
+      cp_async_wait<kS - 1>();  // this lane's pieces of chunk jc landed
+      __syncwarp();             // ... and every other lane's
+      const unsigned char *stg = T.stages + (warp * kS + g % kS) * sbytes;
+      constexpr unsigned RB = Ring<R>::kRB;
+      lc = reinterpret_cast<const uint16_t *>(stg)[kk];
+      x = reinterpret_cast<const R *>(stg + 64)[kk];
+      y = reinterpret_cast<const R *>(stg + 64 + RB)[kk];
+      ux = reinterpret_cast<const R *>(stg + 64 + 2 * RB)[kk];
+      uy = reinterpret_cast<const R *>(stg + 64 + 3 * RB)[kk];
+      uz = reinterpret_cast<const R *>(stg + 64 + 4 * RB)[kk];
+      unsigned o = 64 + 5 * RB;
+      if (has_w && I.w) {
+        w = reinterpret_cast<const R *>(stg + o)[kk];
+        o += RB;
+      }
+      if (has_id && I.id) pid = reinterpret_cast<const int *>(stg + o)[kk];
+    } else {
+      const int p = base + c0 + kk;
+      lc = __ldcs(I.cell + p);
+      x = __ldcs(I.x + p);
+      y = __ldcs(I.y + p);
+      ux = __ldcs(I.ux + p);
+      uy = __ldcs(I.uy + p);
+      uz = __ldcs(I.uz + p);
+      if (has_w && I.w) w = __ldcs(I.w + p);
+      if (has_id && I.id) pid = __ldcs(I.id + p);
+    }
+    const R wd = valid ? w : R(0);
+    int lx = lc & 255, ly = lc >> 8;
+    if (lx >= tw || ly >= th) {
+      // never produced by the library's own kernels: record it and keep
+      // the shared-memory accesses inside the tile
+      atomicOr(&st->error, ERR_STORE);
+      atomicMin(&st->err_step, T.step);
+      lx = min(lx, tw - 1);
+      ly = min(ly, th - 1);
+    }
+
+    // ---- stage 1: bilinear gather on the staggered grid ----
+    // node-centred axis: cell l, weight o; half-staggered axis: cell l-1
+    // with weight o+1/2 if o < 1/2, else cell l with weight o-1/2
+    const bool xl = x < R(0.5), yl = y < R(0.5);
+    const R whx = xl ? x + R(0.5) : x - R(0.5);
+    const R why = yl ? y + R(0.5) : y - R(0.5);
+    const int i_nn = (ly + 1) * CW + (lx + 1);
+    const int i_hn = i_nn - (xl ? 1 : 0);
+    const int i_nh = i_nn - (yl ? CW : 0);
+    const int i_hh = i_hn - (yl ? CW : 0);
+    const R ex = interp(cEx, i_hn, whx, y);
+    const R ey = interp(cEy, i_nh, x, why);
+    const R ez = interp(cEz, i_nn, x, y);
+    const R bx = interp(cBx, i_nh, x, why);
+    const R by = interp(cBy, i_hn, whx, y);
+    const R bz = interp(cBz, i_hh, whx, why);
+
+    // ---- stage 2: relativistic Boris ----
+    const R umx = ux + hq * ex, umy = uy + hq * ey, umz = uz + hq * ez;
+    const R rg = rsqrt_r<R>(R(1) + umx * umx + umy * umy + umz * umz);
+    const R tx = hq * bx * rg, ty = hq * by * rg, tz = hq * bz * rg;
+    const R sf = fdiv<R>(R(2), R(1) + tx * tx + ty * ty + tz * tz);
+    const R upx = umx + (umy * tz - umz * ty);
+    const R upy = umy + (umz * tx - umx * tz);
+    const R upz = umz + (umx * ty - umy * tx);
+    ux = umx + sf * (upy * tz - upz * ty) + hq * ex;
+    uy = umy + sf * (upz * tx - upx * tz) + hq * ey;
+    uz = umz + sf * (upx * ty - upy * tx) + hq * ez;
+
+    // ---- stage 2b: move (at most one cell, CFL) ----
+    const R u2 = ux * ux + uy * uy + uz * uz;
+    const R rgn = rsqrt_r<R>(R(1) + u2);
+    if (T.do_energy) kin += wd * u2 * fdiv<R>(rgn, R(1) + rgn);
+    const R x1 = x + T.dt_dx * ux * rgn;
+    const R y1 = y + T.dt_dy * uy * rgn;
+    const PathSplit<R> ps = split_path(x, y, x1, y1);
+
+    // ---- stage 3: charge-conserving deposit, segment in the start cell ----
+    const R qz = q00 * wd * uz * rgn;
+    {
+      const R bx1 = ps.cut ? (ps.xfirst ? ps.xb : ps.x_sy) : ps.xf;
+      const R by1 = ps.cut ? (ps.xfirst ? ps.x_sx_y : ps.yb) : ps.yf;
+      dep_seg(T.jt, JW, JP, lx, ly, x, y, bx1, by1, ps.s1, qx0 * wd,
+              qy0 * wd, qz);
+    }
+    // the rest of a crossing path waits in the warp's queue
+    const bool need = valid && ps.cut;
+    const unsigned mq = __ballot_sync(0xffffffffu, need);
+    if (mq) {
+      if (need)
+        queue_put(T.q, (qtail + __popc(mq & lt)) & (kQ - 1), lx, ly, x, y, x1,
+                  y1, wd, qz);
+      qtail += __popc(mq);
+      // the ring holds kQ = 64: before each put at most 31 entries wait,
+      // a put adds at most 32, and a full run of 32 is drained at once
+      __syncwarp();
+      if (qtail - qhead >= 32) {
+        queue_take(T.q, T.jt, JW, JP, (qhead + lane) & (kQ - 1), qx0, qy0);
+        qhead += 32;
+        __syncwarp();
+      }
+    }
+
+    // ---- new cell: window shift, boundaries, tile membership ----
+    int nix = T.x0 + lx + ps.di - T.shift;
+    const int niy = wrap1(T.y0 + ly + ps.dj, T.ny);
+    bool removed = false;
+    if (open_x)  // leaves the window it moved in, or the shifted window
+      removed = nix + T.shift >= T.nx || nix < 0;
+    else
+      nix = wrap1(nix, T.nx);
+    const int nlx = nix - T.x0, nly = niy - T.y0;
+    const bool inside =
+        (unsigned)nlx < (unsigned)tw && (unsigned)nly < (unsigned)th;
+    const bool stay = valid && !removed && inside;
+    const bool leave = valid && !removed && !inside;
+    if (valid && removed) ++n_removed;
+
+    // ---- output: stayers to this tile's segment of the other copy,
+    // leavers (global cell) to the tile's outbox ----
+    const unsigned bs = __ballot_sync(0xffffffffu, stay);
+    const unsigned bl = __ballot_sync(0xffffffffu, leave);
+    int sb = 0, lb = 0;
+    if (lane == 0) {
+      if (bs) sb = atomicAdd(&T.s_slots[0], __popc(bs));
+      if (bl) lb = atomicAdd(&T.s_slots[1], __popc(bl));
+    }
+    sb = __shfl_sync(0xffffffffu, sb, 0);
+    lb = __shfl_sync(0xffffffffu, lb, 0);
+    if (stay) {
+      const int d = base + sb + __popc(bs & lt);
+      __stcs(O.cell + d, local_cell(nlx, nly));
+      __stcs(O.x + d, ps.xf);
+      __stcs(O.y + d, ps.yf);
+      __stcs(O.ux + d, ux);
+      __stcs(O.uy + d, uy);
+      __stcs(O.uz + d, uz);
+      if (has_w && O.w) __stcs(O.w + d, w);
+      if (has_id && O.id) __stcs(O.id + d, pid);
+    } else if (leave) {
+      park_leaver(P, ovf, st, T.tile, lb + __popc(bl & lt), T.sim, s, T.step,
+                  nix, niy, ps.xf, ps.yf, ux, uy, uz, w, pid,
+                  has_w && O.w != nullptr, has_id && O.id != nullptr);
+    }
+  }
+  // segments still waiting in the warp's queue
+  __syncwarp();
+  if (lane < qtail - qhead)
+    queue_take(T.q, T.jt, JW, JP, (qhead + lane) & (kQ - 1), qx0, qy0);
+  if (n_removed) atomicAdd(&S.removed[s], n_removed);
+  if (T.do_energy)
+    block_sum_store<R>((double)kin,
+                       &S.part_kin[(size_t)T.tile * kMaxSpecies + s], T.red);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    P.cnt[T.tile] = T.s_slots[0];
+    P.ob_cnt[T.tile] = min(T.s_slots[1], P.ob_cap);
+  }
+}
+
+// The work of one CTA on one tile; CUR = step & 1 selects the field and
+// particle copies, as a compile-time value so that every descriptor access
+// has a constant offset.  kSpec: the single-simulation 16 x 16 FP32 kernel,
+// whose species loops are also specialised on layout and boundary.
+template <typename R, bool kBatch, int TXC, int TYC, int CUR>
+__device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
+                                          const int tile, const int step,
+                                          BatchStatus *st,
+                                          const OverflowDev<R> &ovf,
+                                          unsigned char *smem_raw,
+                                          int *s_slots, double *red) {
+  constexpr bool kSpec = sizeof(R) == 4 && !kBatch && TXC == 16 && TYC == 16;
   const int nx = S.nx, ny = S.ny, ld = S.ld;
   const int TX = TXC > 0 ? TXC : S.tx, TY = TYC > 0 ? TYC : S.ty;
   const int open_x = S.open_x, nsp = S.nsp;
-  const R dt_dx = S.dt_dx, dt_dy = S.dt_dy;
   const int tcx = tile % S.ntx, tcy = tile / S.ntx;
   const int x0 = tcx * TX, y0 = tcy * TY;
-  const int tw = min(TX, nx - x0), th = min(TY, ny - y0);
-  const int cur = step & 1;
 
-  // shared layout: 6 field planes (FW x FH) then 3 current planes (JW x JH)
-  const int FW = TX + 2, FH = TY + 2, FP = FW * FH;
-  const int JW = TX + 3, JH = TY + 3, JP = JW * JH;
-  R *fs = reinterpret_cast<R *>(smem_raw);
-  TileJ<R> jt;
+  TileCtx<R> T;
+  T.CW = TX + 1;
+  T.CP = T.CW * (TY + 1);
+  T.JW = TX + 3;
+  T.JP = T.JW * (TY + 3);
+  const int FW = TX + 2, FP = FW * (TY + 2);
+  const int CW = T.CW, CP = T.CP, JW = T.JW, JP = T.JP;
+  const PushSmem<R> L(TX, TY, false);  // offsets up to the ring
+  Coef4<R> *cf = reinterpret_cast<Coef4<R> *>(smem_raw + L.coef);
+  T.cf = cf;
   if constexpr (sizeof(R) == 4) {
-    jt.hi = reinterpret_cast<int *>(fs + 6 * FP);
-    jt.lo = jt.hi + 3 * JP;
+    T.jt.hi = reinterpret_cast<int *>(smem_raw + L.j);
+    T.jt.lo = T.jt.hi + 3 * JP;
+    T.jt.cnt = reinterpret_cast<int *>(smem_raw + L.cnt);
   } else {
-    jt.v = reinterpret_cast<double *>(fs + 6 * FP);
+    T.jt.v = reinterpret_cast<double *>(smem_raw + L.j);
   }
-  SegQueue<R> q;
-  {
-    // queues after the current planes (8 bytes per value), 16-byte aligned
-    const size_t qoff =
-        ((sizeof(R) * 6 * FP + 8 * 3 * (size_t)JP) + 15) & ~size_t(15);
-    unsigned char *qb = smem_raw + qoff;
-    const int wq = threadIdx.x >> 5;
-    q.v = reinterpret_cast<R *>(qb) + wq * 8 * kQ;
-    q.cell = reinterpret_cast<int *>(qb + sizeof(R) * 8 * kQ * kWarps) +
-             wq * kQ;
-  }
+  const int warp = threadIdx.x >> 5;
+  T.q.v = reinterpret_cast<R *>(smem_raw + L.q) + warp * kQVals * kQ;
+  T.q.cell = reinterpret_cast<int *>(smem_raw + L.q +
+                                     sizeof(R) * kQVals * kQ * kWarps) +
+             warp * kQ;
+  T.stages = smem_raw + L.stages;
+  T.x0 = x0;
+  T.y0 = y0;
+  T.tw = min(TX, nx - x0);
+  T.th = min(TY, ny - y0);
+  T.nx = nx;
+  T.ny = ny;
+  T.tile = tile;
+  T.sim = sim;
+  T.step = step;
+  T.dt_dx = S.dt_dx;
+  T.dt_dy = S.dt_dy;
+  T.s_slots = s_slots;
+  T.red = red;
 
+  // ---- stage 0: fields of the tile + one guard cell, coefficient form ----
+  R *raw = reinterpret_cast<R *>(smem_raw + L.q);
   for (int k = threadIdx.x; k < 6 * FP; k += blockDim.x) {
     const int c = k / FP, r = k - c * FP;
     const int lj = r / FW, li = r - lj * FW;
-    const R *src = c < 3 ? S.E[cur][c] : S.B[cur][c - 3];
+    const R *src = c < 3 ? S.E[CUR][c] : S.B[CUR][c - 3];
     int gi = x0 - 1 + li;
     const int gj = wrap1(y0 - 1 + lj, ny);
     R v = R(0);
@@ -261,263 +751,50 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
       gi = wrap1(gi, nx);
       v = src[(size_t)gj * ld + gi];
     }
-    fs[k] = v;
+    raw[k] = v;
   }
-  jt.zero(3 * JP);
+  T.jt.zero(JP);
+  __syncthreads();
+  for (int k = threadIdx.x; k < 6 * CP; k += blockDim.x) {
+    const int c = k / CP, r = k - c * CP;
+    const int cj = r / CW, ci = r - cj * CW;
+    const R *f = raw + c * FP + cj * FW + ci;
+    const R f00 = f[0], f10 = f[1], f01 = f[FW], f11 = f[FW + 1];
+    Coef4<R> v;
+    v.a = f00;
+    v.b = f10 - f00;
+    v.c = f01 - f00;
+    v.d = (f11 - f10) - v.c;
+    cf[k] = v;
+  }
+  // (the species loop's barrier separates these reads of the staging area
+  // from the queue writes)
   const int nsh = S.moving_window ? *S.n_shift : 0;
-  const int shift = shift_due(S, step, nsh) ? 1 : 0;
-  const bool do_energy =
-      S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
+  T.shift = shift_due(S, step, nsh) ? 1 : 0;
+  T.do_energy = S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
 
-  const R *Ex = fs, *Ey = fs + FP, *Ez = fs + 2 * FP;
-  const R *Bx = fs + 3 * FP, *By = fs + 4 * FP, *Bz = fs + 5 * FP;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-
+  unsigned g = 0;  // chunks this warp has taken through the particle ring
   for (int s = 0; s < nsp; ++s) {
-    const SpeciesDev<R> &P = S.sp[s];
-    const Planes<R> &I = P.buf[cur];
-    const Planes<R> &O = P.buf[cur ^ 1];
-    const R hq = P.hq, qx0 = P.dq[0], qy0 = P.dq[1], q00 = P.dq[2];
-    const int n = P.cnt[tile];
-    const int base = P.off[tile];
-    const int ob_cap = P.ob_cap;
-    if (threadIdx.x == 0) {
-      s_slots[0] = 0;
-      s_slots[1] = 0;
-    }
-    __syncthreads();  // also: fields staged, J tile zeroed
-    int n_removed = 0;
-    int qhead = 0, qtail = 0;  // warp-uniform ring indices
-    R kin = R(0);
-    // warps work independently on chunks of 32 particles: no block barrier
-    // inside the loop; each warp claims its output slots with one atomic
-    for (int c0 = warp * 32; c0 < n; c0 += blockDim.x) {
-      const int k = c0 + lane;
-      const bool valid = k < n;
-      // invalid lanes carry a particle at rest in the tile's first cell and
-      // never deposit or store
-      int lc = 0, pid = 0;
-      R x = R(0.5), y = R(0.5), ux = R(0), uy = R(0), uz = R(0), w = R(1);
-      if (valid) {
-        const int p = base + k;
-        lc = __ldcs(I.cell + p);
-        x = __ldcs(I.x + p);
-        y = __ldcs(I.y + p);
-        ux = __ldcs(I.ux + p);
-        uy = __ldcs(I.uy + p);
-        uz = __ldcs(I.uz + p);
-        if (I.w) w = __ldcs(I.w + p);
-        if (I.id) pid = __ldcs(I.id + p);
-      }
-      int lx = lc & 255, ly = lc >> 8;
-      if (lx >= tw || ly >= th) {
-        // never produced by the library's own kernels: record it and keep
-        // the shared-memory accesses inside the tile
-        atomicOr(&st->error, ERR_STORE);
-        atomicMin(&st->err_step, step);
-        lx = min(lx, tw - 1);
-        ly = min(ly, th - 1);
-      }
-
-      // ---- stage 1: bilinear gather on the staggered grid ----
-      // node-centred axis: cell l, weight o; half-staggered axis: cell l-1
-      // with weight o+1/2 if o < 1/2, else cell l with weight o-1/2
-      const bool xl = x < R(0.5), yl = y < R(0.5);
-      const R whx = xl ? x + R(0.5) : x - R(0.5);
-      const R why = yl ? y + R(0.5) : y - R(0.5);
-      const int b_nn = (ly + 1) * FW + (lx + 1);
-      const int b_hn = b_nn - (xl ? 1 : 0);
-      const int b_nh = b_nn - (yl ? FW : 0);
-      const int b_hh = b_hn - (yl ? FW : 0);
-#define ZP_BILIN(F, b, wx, wy)                                               \
-  ((R(1) - (wy)) * ((R(1) - (wx)) * (F)[b] + (wx) * (F)[(b) + 1]) +          \
-   (wy) * ((R(1) - (wx)) * (F)[(b) + FW] + (wx) * (F)[(b) + FW + 1]))
-      const R ex = ZP_BILIN(Ex, b_hn, whx, y);
-      const R ey = ZP_BILIN(Ey, b_nh, x, why);
-      const R ez = ZP_BILIN(Ez, b_nn, x, y);
-      const R bx = ZP_BILIN(Bx, b_nh, x, why);
-      const R by = ZP_BILIN(By, b_hn, whx, y);
-      const R bz = ZP_BILIN(Bz, b_hh, whx, why);
-#undef ZP_BILIN
-
-      // ---- stage 2: relativistic Boris ----
-      const R umx = ux + hq * ex, umy = uy + hq * ey, umz = uz + hq * ez;
-      const R rg = rsqrt_r<R>(R(1) + umx * umx + umy * umy + umz * umz);
-      const R tx = hq * bx * rg, ty = hq * by * rg, tz = hq * bz * rg;
-      const R sf = fdiv<R>(R(2), R(1) + tx * tx + ty * ty + tz * tz);
-      const R upx = umx + (umy * tz - umz * ty);
-      const R upy = umy + (umz * tx - umx * tz);
-      const R upz = umz + (umx * ty - umy * tx);
-      ux = umx + sf * (upy * tz - upz * ty) + hq * ex;
-      uy = umy + sf * (upz * tx - upx * tz) + hq * ey;
-      uz = umz + sf * (upx * ty - upy * tx) + hq * ez;
-
-      // ---- stage 2b: move (at most one cell, CFL) ----
-      const R u2 = ux * ux + uy * uy + uz * uz;
-      const R rgn = rsqrt_r<R>(R(1) + u2);
-      if (do_energy && valid) kin += w * u2 * fdiv<R>(rgn, R(1) + rgn);
-      R x1 = x + dt_dx * ux * rgn;
-      R y1 = y + dt_dy * uy * rgn;
-      R xf, yf;
-      const int di = axis_cross(x1, xf);
-      const int dj = axis_cross(y1, yf);
-
-      // ---- stage 3: charge-conserving deposit ----
-      // The straight path from (x, y) to (x1, y1) (start-cell frame) is cut
-      // where it meets the x face xb (parameter sx) and the y face yb (sy);
-      // s1 = min, s2 = max (an exact tie counts as x first).  Segment 1 lies
-      // in the start cell, segment 2 in the cell entered at s1, segment 3 in
-      // the final cell; each is written in its own cell's frame and the last
-      // one ends at the stored offsets (xf, yf).  Empty segments are skipped
-      // per lane; a warp skips a segment that none of its lanes needs.
-      const R qx = qx0 * w, qy = qy0 * w, qz = q00 * w * uz * rgn;
-      const R xb = di > 0 ? R(1) : R(0);
-      const R yb = dj > 0 ? R(1) : R(0);
-      const R sx = di ? fdiv<R>(xb - x, x1 - x) : R(1);
-      const R sy = dj ? fdiv<R>(yb - y, y1 - y) : R(1);
-      const bool xfirst = sx <= sy;
-      const R s1 = xfirst ? sx : sy, s2 = xfirst ? sy : sx;
-      const R y_sx = y + sx * (y1 - y);  // where the path meets the x face
-      const R x_sy = x + sy * (x1 - x);  // where it meets the y face
-      const bool cut = (di | dj) != 0;
-      const bool two = di != 0 && dj != 0;
-      {
-        const R bx1 = cut ? (xfirst ? xb : x_sy) : xf;
-        const R by1 = cut ? (xfirst ? y_sx : yb) : yf;
-        if (valid) dep_seg(jt, JW, JP, lx, ly, x, y, bx1, by1, s1, qx, qy, qz);
-      }
-      // segments outside the start cell wait in the warp's queue
-      const bool need2 = valid && cut, need3 = valid && two;
-      const unsigned m2 = __ballot_sync(0xffffffffu, need2);
-      if (m2) {
-        if (need2) {
-          const int c2x = xfirst ? di : 0, c2y = xfirst ? 0 : dj;
-          const R ax2 = xfirst ? xb - R(di) : x_sy;
-          const R ay2 = xfirst ? y_sx : yb - R(dj);
-          const R bx2 = two ? (xfirst ? x_sy - R(di) : xb) : xf;
-          const R by2 = two ? (xfirst ? yb : y_sx - R(dj)) : yf;
-          queue_put(q, (qtail + __popc(m2 & lt)) & (kQ - 1), lx + c2x,
-                    ly + c2y, ax2, ay2, bx2, by2, s2 - s1, qx, qy, qz);
-        }
-        qtail += __popc(m2);
-        // the ring holds kQ = 64: before each put at most 31 entries wait,
-        // a put adds at most 32, and a full run of 32 is drained at once
-        __syncwarp();
-        if (qtail - qhead >= 32) {
-          queue_take(q, jt, JW, JP, (qhead + lane) & (kQ - 1));
-          qhead += 32;
-          __syncwarp();
-        }
-        const unsigned m3 = __ballot_sync(0xffffffffu, need3);
-        if (m3) {
-          if (need3) {
-            const R ax3 = xfirst ? x_sy - R(di) : xb - R(di);
-            const R ay3 = xfirst ? yb - R(dj) : y_sx - R(dj);
-            queue_put(q, (qtail + __popc(m3 & lt)) & (kQ - 1), lx + di,
-                      ly + dj, ax3, ay3, xf, yf, R(1) - s2, qx, qy, qz);
-          }
-          qtail += __popc(m3);
-          __syncwarp();
-          if (qtail - qhead >= 32) {
-            queue_take(q, jt, JW, JP, (qhead + lane) & (kQ - 1));
-            qhead += 32;
-            __syncwarp();
-          }
-        }
-      }
-
-      // ---- new cell: window shift, boundaries, tile membership ----
-      int nix = x0 + lx + di - shift;
-      const int niy = wrap1(y0 + ly + dj, ny);
-      bool removed = false;
-      if (open_x)  // leaves the window it moved in, or the shifted window
-        removed = nix + shift >= nx || nix < 0;
+    if constexpr (kSpec) {
+      const Planes<R> &I = S.sp[s].buf[CUR];
+      const bool plain = I.w == nullptr && I.id == nullptr;
+      if (plain && open_x)
+        push_species<R, CUR, true, true, true>(S, s, T, g, st, ovf);
+      else if (plain)
+        push_species<R, CUR, true, true, false>(S, s, T, g, st, ovf);
       else
-        nix = wrap1(nix, nx);
-      const int nlx = nix - x0, nly = niy - y0;
-      const bool inside = (unsigned)nlx < (unsigned)tw && (unsigned)nly < (unsigned)th;
-      const bool stay = valid && !removed && inside;
-      const bool leave = valid && !removed && !inside;
-      if (valid && removed) ++n_removed;
-
-      // ---- output: stayers to this tile's segment of the other copy,
-      // leavers (global cell) to the tile's outbox ----
-      const unsigned bs = __ballot_sync(0xffffffffu, stay);
-      const unsigned bl = __ballot_sync(0xffffffffu, leave);
-      int sb = 0, lb = 0;
-      if (lane == 0) {
-        if (bs) sb = atomicAdd(&s_slots[0], __popc(bs));
-        if (bl) lb = atomicAdd(&s_slots[1], __popc(bl));
-      }
-      sb = __shfl_sync(0xffffffffu, sb, 0);
-      lb = __shfl_sync(0xffffffffu, lb, 0);
-      if (stay) {
-        const int d = base + sb + __popc(bs & lt);
-        __stcs(O.cell + d, local_cell(nlx, nly));
-        __stcs(O.x + d, xf);
-        __stcs(O.y + d, yf);
-        __stcs(O.ux + d, ux);
-        __stcs(O.uy + d, uy);
-        __stcs(O.uz + d, uz);
-        if (O.w) __stcs(O.w + d, w);
-        if (O.id) __stcs(O.id + d, pid);
-      } else if (leave) {
-        const int slot = lb + __popc(bl & lt);
-        if (slot < ob_cap) {
-          const size_t d = (size_t)tile * ob_cap + slot;
-          P.ob_ix[d] = nix;
-          P.ob_iy[d] = niy;
-          P.ob_x[d] = xf;
-          P.ob_y[d] = yf;
-          P.ob_ux[d] = ux;
-          P.ob_uy[d] = uy;
-          P.ob_uz[d] = uz;
-          if (O.w) P.ob_w[d] = w;
-          if (O.id) P.ob_id[d] = pid;
-        } else {
-          const int o = atomicAdd(&st->ovf_count, 1);
-          if (o < ovf.cap) {
-            ovf.sim[o] = it.x;
-            ovf.species[o] = s;
-            ovf.ix[o] = nix;
-            ovf.iy[o] = niy;
-            ovf.x[o] = xf;
-            ovf.y[o] = yf;
-            ovf.ux[o] = ux;
-            ovf.uy[o] = uy;
-            ovf.uz[o] = uz;
-            ovf.w[o] = w;
-            ovf.id[o] = pid;
-            atomicOr(&st->error, ERR_OVERFLOW);
-          } else {
-            atomicAdd(&st->lost, 1);
-            atomicOr(&st->error, ERR_LOST);
-          }
-          atomicMin(&st->err_step, step);
-        }
-      }
-    }
-    // segments still waiting in the warp's queue
-    __syncwarp();
-    if (lane < qtail - qhead)
-      queue_take(q, jt, JW, JP, (qhead + lane) & (kQ - 1));
-    if (n_removed) atomicAdd(&S.removed[s], n_removed);
-    if (do_energy)
-      block_sum_store<R>((double)kin,
-                         &S.part_kin[(size_t)tile * kMaxSpecies + s], red);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      P.cnt[tile] = s_slots[0];
-      P.ob_cnt[tile] = min(s_slots[1], ob_cap);
+        push_species<R, CUR, false, false, false>(S, s, T, g, st, ovf);
+    } else {
+      push_species<R, CUR, false, false, false>(S, s, T, g, st, ovf);
     }
   }
   __syncthreads();
 
   // ---- stage 3b: fold the tile's current (with guards) into global J ----
   for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) {
-    if (!jt.nonzero(k)) continue;
     const int c = k / JP, r = k - c * JP;
+    double v;
+    if (!T.jt.value(c, r, JW, JP, v)) continue;
     const int lj = r / JW, li = r - lj * JW;
     int gi = x0 - 1 + li;
     const int gj = wrap1(y0 - 1 + lj, ny);
@@ -526,19 +803,39 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
     } else {
       gi = wrap1(gi, nx);
     }
-    atomicAdd(S.J[cur][c] + (size_t)gj * ld + gi, (R)(jt.value(k) * S.jscale[c]));
+    atomicAdd(S.J[CUR][c] + (size_t)gj * ld + gi, (R)(v * S.jscale[c]));
   }
 }
 
+// kBatch = false: one simulation, its descriptor passed as a grid-constant
+// kernel parameter; kBatch = true: descriptors of many simulations read from
+// device memory.  TXC, TYC > 0: tile size fixed at compile time (shared-
+// memory offsets become immediates); 0: taken from the descriptor.
+template <typename R, bool kBatch, int TXC, int TYC>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
+    push_deposit_kernel(const SimDev<R> *__restrict__ sims,
+                        const __grid_constant__ SimDev<R> one,
+                        const int2 *__restrict__ items, BatchStatus *st,
+                        const __grid_constant__ OverflowDev<R> ovf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_slots[2];  // stayers written, leavers written
+  __shared__ double red[kWarps];
+
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const int2 it = items[blockIdx.x];
+  const SimDev<R> &S = kBatch ? sims[it.x] : one;
+  if (step & 1)
+    push_tile<R, kBatch, TXC, TYC, 1>(S, it.x, it.y, step, st, ovf, smem_raw,
+                                      s_slots, red);
+  else
+    push_tile<R, kBatch, TXC, TYC, 0>(S, it.x, it.y, step, st, ovf, smem_raw,
+                                      s_slots, red);
+}
+
 template <typename R>
-size_t push_smem_bytes(int tx, int ty) {
-  // 6 field planes of R, then 3 current planes of 8 bytes (two int32 words
-  // in FP32, one double in FP64), then (16-byte aligned) per warp a queue of
-  // kQ segments of 8 R + 1 int
-  const size_t head = sizeof(R) * 6 * (size_t)(tx + 2) * (ty + 2) +
-                      8 * 3 * (size_t)(tx + 3) * (ty + 3);
-  return ((head + 15) & ~size_t(15)) +
-         (size_t)kWarps * kQ * (8 * sizeof(R) + sizeof(int));
+size_t push_smem_bytes(int tx, int ty, bool wide) {
+  return PushSmem<R>(tx, ty, wide).total;
 }
 
 template <typename R, bool kBatch>
@@ -552,8 +849,8 @@ static cudaError_t set_push_smem(int smem) {
 }
 
 template <typename R>
-cudaError_t prepare_push_deposit(int max_tx, int max_ty) {
-  const int smem = (int)push_smem_bytes<R>(max_tx, max_ty);
+cudaError_t prepare_push_deposit(int max_tx, int max_ty, bool wide) {
+  const int smem = (int)push_smem_bytes<R>(max_tx, max_ty, wide);
   cudaError_t e = set_push_smem<R, false>(smem);
   if (e != cudaSuccess) return e;
   return set_push_smem<R, true>(smem);
@@ -562,11 +859,11 @@ cudaError_t prepare_push_deposit(int max_tx, int max_ty) {
 template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
-                                int max_ty, bool all16, BatchStatus *st,
-                                const OverflowDev<R> &ovf,
+                                int max_ty, bool all16, bool wide,
+                                BatchStatus *st, const OverflowDev<R> &ovf,
                                 cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
-  const size_t smem = push_smem_bytes<R>(max_tx, max_ty);
+  const size_t smem = push_smem_bytes<R>(max_tx, max_ty, wide);
   // the 16 x 16 kernel needs every simulation of the batch to use 16 x 16
   // tiles (ragged edge tiles are fine)
   const bool t16 = all16;
@@ -588,20 +885,20 @@ cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
   return cudaGetLastError();
 }
 
-template size_t push_smem_bytes<float>(int, int);
-template size_t push_smem_bytes<double>(int, int);
-template cudaError_t prepare_push_deposit<float>(int, int);
-template cudaError_t prepare_push_deposit<double>(int, int);
+template size_t push_smem_bytes<float>(int, int, bool);
+template size_t push_smem_bytes<double>(int, int, bool);
+template cudaError_t prepare_push_deposit<float>(int, int, bool);
+template cudaError_t prepare_push_deposit<double>(int, int, bool);
 template cudaError_t launch_push_deposit<float>(const SimDev<float> *,
                                                 const SimDev<float> *,
                                                 const int2 *, int, int, int,
-                                                bool, BatchStatus *,
+                                                bool, bool, BatchStatus *,
                                                 const OverflowDev<float> &,
                                                 cudaStream_t);
 template cudaError_t launch_push_deposit<double>(const SimDev<double> *,
                                                  const SimDev<double> *,
                                                  const int2 *, int, int, int,
-                                                 bool, BatchStatus *,
+                                                 bool, bool, BatchStatus *,
                                                  const OverflowDev<double> &,
                                                  cudaStream_t);
 

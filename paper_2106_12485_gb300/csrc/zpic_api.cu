@@ -321,6 +321,10 @@ class Batch : public BatchBase {
         sticky_ = fail(ZPIC_EOVERFLOW, "particle storage exhausted");
         return sticky_;
       }
+      if (st.error & ERR_TIMEOUT) {
+        sticky_ = fail(ZPIC_ETIMEOUT, "a bounded wait for a particle copy gave up");
+        return sticky_;
+      }
       if (st.error & ERR_STORE) {
         sticky_ = fail(ZPIC_ECUDA, "particle store corrupted (particle outside its tile)");
         return sticky_;
@@ -676,7 +680,7 @@ class Batch : public BatchBase {
     S.dt = c.dt;
     S.tx = std::min(c.tile_x ? c.tile_x : 16, c.nx);
     S.ty = std::min(c.tile_y ? c.tile_y : 16, c.ny);
-    if (push_smem_bytes<R>(S.tx, S.ty) > 200 * 1024)
+    if (push_smem_bytes<R>(S.tx, S.ty, true) > 226 * 1024)
       return fail(ZPIC_EINVAL, "tile too large for shared memory");
     S.ntx = (S.nx + S.tx - 1) / S.tx;
     S.nty = (S.ny + S.ty - 1) / S.ty;
@@ -1176,6 +1180,13 @@ class Batch : public BatchBase {
   // ---- launch sequence ---------------------------------------------------------
 
   const SimDev<R> *dsims() const { return (const SimDev<R> *)sims_dev_.p; }
+  // some species of some simulation stores weights or ids
+  bool ring_wide() const {
+    for (const auto &S : sims_)
+      for (const auto &P : S.sp)
+        if (P.has_w || P.has_id) return true;
+    return false;
+  }
   BatchStatus *dst() const { return (BatchStatus *)st_mem_.p; }
 
   cudaError_t launch_stage(int k) {
@@ -1183,7 +1194,8 @@ class Batch : public BatchBase {
       case 0:
         return launch_push_deposit<R>(dsims(), n_sims == 1 ? &sims_[0].dev : nullptr,
                                       (const int2 *)items_.p, n_items_,
-                                      max_tx_, max_ty_, all16_, dst(), ovf_,
+                                      max_tx_, max_ty_, all16_, ring_wide(),
+                                      dst(), ovf_,
                                       stream_);
       case 1:
         return launch_yee<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
@@ -1203,7 +1215,7 @@ class Batch : public BatchBase {
   int enqueue(int n) {
     if (n == 0) return ZPIC_OK;
     if (profiling_) {
-      ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_));
+      ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_, ring_wide()));
       if (timers_.empty())
         for (int k = 0; k < 4; ++k) {
           timers_.emplace_back();
@@ -1228,7 +1240,7 @@ class Batch : public BatchBase {
 
   int capture() {
     // kernel attributes are set outside the capture
-    ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_));
+    ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_, ring_wide()));
     cudaStream_t cs;
     ZP_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t keep = stream_;

@@ -10,13 +10,15 @@ namespace zp {
 constexpr int kYeeX = 32;
 constexpr int kYeeY = 8;
 
+// Dynamic shared memory of the push kernel for tx x ty tiles; wide: some
+// species stores weights or ids (larger particle-copy stages).
 template <typename R>
-size_t push_smem_bytes(int tx, int ty);
+size_t push_smem_bytes(int tx, int ty, bool wide);
 
 // Sets the push kernel's dynamic shared-memory limit (call before launching
 // or capturing it).
 template <typename R>
-cudaError_t prepare_push_deposit(int max_tx, int max_ty);
+cudaError_t prepare_push_deposit(int max_tx, int max_ty, bool wide);
 
 // Stages 1-3 over all (sim, tile) items.  `single` (host copy of the only
 // descriptor, or null for a batch) selects the one-simulation kernel that
@@ -24,7 +26,8 @@ cudaError_t prepare_push_deposit(int max_tx, int max_ty);
 template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
-                                int max_ty, bool all16, BatchStatus *st,
+                                int max_ty, bool all16, bool wide,
+                                BatchStatus *st,
                                 const OverflowDev<R> &ovf,
                                 cudaStream_t stream);
 

@@ -40,12 +40,9 @@ def empty_load():
             "id": np.zeros(0, np.int32)}
 
 
-def test_lwfa_window_laser_injection_parity():
-    # 400 steps: the plasma entering through the window reaches the laser
-    # (about 300 cells behind the right edge) and carries real currents;
-    # before that its displacements are below the FP32 offset resolution
-    nx, ny, steps = 512, 32, 400
-    cfg = W.lwfa(nx=nx, ny=ny, track_ids=True, energy_every=10)
+def lwfa_pair(nx, ny, steps, precision):
+    cfg = W.lwfa(nx=nx, ny=ny, track_ids=True, energy_every=10,
+                 precision=precision)
     Lx = nx * 0.02
     gpu = Z.Sim(cfg)
     window = {"species": [{"ppc_x": 2, "ppc_y": 2, "ramp_x0": Lx,
@@ -55,20 +52,48 @@ def test_lwfa_window_laser_injection_parity():
                            cap_extra=steps * ny * 4 + 16)
     l = cfg.laser
     orc.laser(l.a0, l.omega0, l.w0, l.fwhm, l.x0, l.y_center)
-    H.compare_fields(gpu, orc, 1e-6, names=H.FIELDS[:6])   # laser init
+    return gpu, orc
+
+
+def check_lwfa(gpu, orc, nx, ny, steps, tol, tol_kin):
     gpu.step(steps)
     orc.step(steps)
-    assert gpu.info().n_shift == orc.n_shift > 350
+    # shifts: (step + 1) dt >= (n + 1) dx with dt / dx = 0.95
+    assert gpu.info().n_shift == orc.n_shift > int(0.9 * steps)
     assert gpu.num_particles(0) == orc.species[0].n > 0
-    H.compare_fields(gpu, orc, 1e-4)
-    H.compare_particles(gpu, orc, 0, nx, ny, 1e-4)
+    H.compare_fields(gpu, orc, tol)
+    H.compare_particles(gpu, orc, 0, nx, ny, tol)
     # energy records agree (laser field energy dominates)
     for (st, wE, wB, kin), (ost, owE, owB, okin) in zip(gpu.energy(),
                                                          orc.history[9::10]):
         assert st == ost
-        assert wE == pytest.approx(owE, rel=1e-4)
-        assert wB == pytest.approx(owB, rel=1e-4)
-        assert kin[0] == pytest.approx(okin[0], rel=1e-3, abs=1e-9 * owE)
+        assert wE == pytest.approx(owE, rel=tol)
+        assert wB == pytest.approx(owB, rel=tol)
+        assert kin[0] == pytest.approx(okin[0], rel=tol_kin, abs=1e-9 * owE)
+
+
+def test_lwfa_window_laser_injection_parity_fp64():
+    # FP64 form: the window, laser, ramp and injection logic against the
+    # oracle at rounding level over 600 steps (the plasma reaches the laser
+    # after about 300 steps and is driven nonlinearly from there on)
+    nx, ny, steps = 512, 32, 600
+    gpu, orc = lwfa_pair(nx, ny, steps, Z.FP64)
+    H.compare_fields(gpu, orc, 1e-12, names=H.FIELDS[:6])   # laser init
+    check_lwfa(gpu, orc, nx, ny, steps, 1e-10, 1e-10)
+
+
+def test_lwfa_window_laser_injection_parity_fp32():
+    # FP32 form over 300 steps, until the plasma that entered through the
+    # window reaches the laser and carries real currents.  Earlier, the
+    # currents of barely moving cold particles are below the FP32 offset
+    # resolution (J is then compared through E and B, which integrate it);
+    # later, the a0 = 2 laser drives the plasma nonlinearly and rounding
+    # differences grow by orders of magnitude within 100 steps, in any
+    # FP32 implementation against an FP64 one
+    nx, ny, steps = 512, 32, 300
+    gpu, orc = lwfa_pair(nx, ny, steps, Z.FP32)
+    H.compare_fields(gpu, orc, 1e-6, names=H.FIELDS[:6])    # laser init
+    check_lwfa(gpu, orc, nx, ny, steps, 1e-4, 1e-3)
 
 
 def batch_configs():
