@@ -28,6 +28,12 @@
 
 namespace zp {
 
+// CTA shape of the push kernel: kPT threads (kPW warps) per tile, and the
+// CTAs per SM that the FP32 register budget is sized for.
+constexpr int kPT = 256;
+constexpr int kPW = kPT / 32;
+constexpr int kPushCtasF32 = 3;
+
 template <typename R>
 __device__ __forceinline__ R rsqrt_r(R v);
 template <>
@@ -360,7 +366,7 @@ __device__ __forceinline__ void block_sum_store(double v, double *dst,
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < kWarps ? red[lane] : 0.0;
+    v = lane < kPW ? red[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) *dst = v;
   }
@@ -432,12 +438,12 @@ struct PushSmem {
     const size_t cnt_bytes = sizeof(R) == 4 ? JP * sizeof(int) : 0;
     q = (cnt + cnt_bytes + 15) & ~size_t(15);
     const size_t qbytes =
-        (size_t)kWarps * kQ * (kQVals * sizeof(R) + sizeof(int));
+        (size_t)kPW * kQ * (kQVals * sizeof(R) + sizeof(int));
     const size_t raw = 6 * (size_t)(tx + 2) * (ty + 2) * sizeof(R);
     ring = (q + (qbytes > raw ? qbytes : raw) + 15) & ~size_t(15);
     constexpr int S = Ring<R>::kStages;
     stages = ring;
-    total = stages + (size_t)kWarps * S * Ring<R>::stage_bytes(wide, wide);
+    total = stages + (size_t)kPW * S * Ring<R>::stage_bytes(wide, wide);
   }
 };
 
@@ -491,9 +497,9 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
 
   // warps work independently on chunks of 32 particles: no block barrier
   // inside the loop; each warp claims its output slots with one atomic.
-  // Chunk jc of warp `warp` starts at particle warp * 32 + jc * kThreads.
+  // Chunk jc of warp `warp` starts at particle warp * 32 + jc * kPT.
   constexpr int kS = Ring<R>::kStages;
-  const int nch = n > warp * 32 ? (n - warp * 32 + kThreads - 1) / kThreads : 0;
+  const int nch = n > warp * 32 ? (n - warp * 32 + kPT - 1) / kPT : 0;
   const unsigned sbytes = Ring<R>::stage_bytes(has_w, has_id);
   const unsigned stg0 = smem_addr(T.stages) + warp * kS * sbytes;
   RingLane rl;
@@ -503,12 +509,12 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
     for (int jc = 0; jc < kS - 1; ++jc) {
       if (jc < nch)
         ring_issue(rl, stg0 + ((g + jc) % kS) * sbytes,
-                   base + warp * 32 + jc * kThreads);
+                   base + warp * 32 + jc * kPT);
       cp_async_commit();
     }
   }
   for (int jc = 0; jc < nch; ++jc, ++g) {
-    const int c0 = warp * 32 + jc * kThreads;
+    const int c0 = warp * 32 + jc * kPT;
     // lanes past the end repeat the last particle with zero weight: they
     // run the same instructions, deposit nothing and store nothing
     const bool valid = c0 + lane < n;
@@ -521,7 +527,7 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
       __syncwarp();
       if (jc + kS - 1 < nch)
         ring_issue(rl, stg0 + ((g + kS - 1) % kS) * sbytes,
-                   c0 + base + (kS - 1) * kThreads);
+                   c0 + base + (kS - 1) * kPT);
       cp_async_commit();
       cp_async_wait<kS - 1>();  // this lane's pieces of chunk jc landed
       __syncwarp();             // ... and every other lane's
@@ -719,7 +725,7 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
   const int warp = threadIdx.x >> 5;
   T.q.v = reinterpret_cast<R *>(smem_raw + L.q) + warp * kQVals * kQ;
   T.q.cell = reinterpret_cast<int *>(smem_raw + L.q +
-                                     sizeof(R) * kQVals * kQ * kWarps) +
+                                     sizeof(R) * kQVals * kQ * kPW) +
              warp * kQ;
   T.stages = smem_raw + L.stages;
   T.x0 = x0;
@@ -812,14 +818,14 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
 // device memory.  TXC, TYC > 0: tile size fixed at compile time (shared-
 // memory offsets become immediates); 0: taken from the descriptor.
 template <typename R, bool kBatch, int TXC, int TYC>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kPT, sizeof(R) == 4 ? kPushCtasF32 : 2)
     push_deposit_kernel(const SimDev<R> *__restrict__ sims,
                         const __grid_constant__ SimDev<R> one,
                         const int2 *__restrict__ items, BatchStatus *st,
                         const __grid_constant__ OverflowDev<R> ovf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slots[2];  // stayers written, leavers written
-  __shared__ double red[kWarps];
+  __shared__ double red[kPW];
 
   const int step = st->step;
   if (frozen(st, step)) return;
@@ -869,17 +875,17 @@ cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
   const bool t16 = all16;
   if (single) {
     if (t16)
-      push_deposit_kernel<R, false, 16, 16><<<n_items, kThreads, smem, stream>>>(
+      push_deposit_kernel<R, false, 16, 16><<<n_items, kPT, smem, stream>>>(
           sims, *single, items, st, ovf);
     else
-      push_deposit_kernel<R, false, 0, 0><<<n_items, kThreads, smem, stream>>>(
+      push_deposit_kernel<R, false, 0, 0><<<n_items, kPT, smem, stream>>>(
           sims, *single, items, st, ovf);
   } else {
     if (t16)
-      push_deposit_kernel<R, true, 16, 16><<<n_items, kThreads, smem, stream>>>(
+      push_deposit_kernel<R, true, 16, 16><<<n_items, kPT, smem, stream>>>(
           sims, SimDev<R>{}, items, st, ovf);
     else
-      push_deposit_kernel<R, true, 0, 0><<<n_items, kThreads, smem, stream>>>(
+      push_deposit_kernel<R, true, 0, 0><<<n_items, kPT, smem, stream>>>(
           sims, SimDev<R>{}, items, st, ovf);
   }
   return cudaGetLastError();
