@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=512,
                     help="cells per side of the oracle sample")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "clouds", "lwfa", "batch",
+                    choices=["uniform", "clouds", "lwfa", "weibel", "batch",
                              "precision"],
                     help="uniform (default): the large uniform plasma; the "
                     "others print one line for that workload")
@@ -313,12 +313,17 @@ def other_workload(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    if args.workload in ("clouds", "lwfa"):
+    if args.workload in ("clouds", "lwfa", "weibel"):
         if args.workload == "clouds":
             cfg = W.clouds(energy_every=10)
             warm = args.warmup
             desc = ("collision of plasma clouds 1024x1024, e-/e+ 4x4 ppc in "
                     "two clouds drifting +-0.2, u_th 0.05, FP32")
+        elif args.workload == "weibel":
+            cfg = W.weibel(energy_every=10)
+            warm = args.warmup
+            desc = ("Weibel: e-/e+ 16x16 ppc each over 512x512 cells, "
+                    "counter-drifting +-0.6 along z, u_th 0.1, FP32")
         else:
             cfg = W.lwfa(energy_every=10)
             warm = max(args.warmup, 2000)   # let the plasma fill the window

@@ -44,7 +44,8 @@ def build(force: bool = False) -> str:
 
 class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double),
-                ("dy", C.c_double), ("dt", C.c_double), ("open_x", C.c_int)]
+                ("dy", C.c_double), ("dt", C.c_double), ("open_x", C.c_int),
+                ("filter_j", C.c_int)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -86,6 +87,7 @@ def lib():
             L.orc_move_deposit.restype = C.c_int
             L.orc_push_deposit.argtypes = [G, F, S, C.c_int, C.c_int, _DP]
             L.orc_yee_b_half.argtypes = [G, F]
+            L.orc_filter_current.argtypes = [G, F]
             L.orc_yee_e.argtypes = [G, F]
             L.orc_field_energy.argtypes = [G, F, _DP, _DP]
             L.orc_laser.argtypes = [G, F] + [C.c_double] * 6
@@ -145,8 +147,9 @@ class Sim:
     """A grid, its fields and its species, advanced by the oracle."""
 
     def __init__(self, nx, ny, dx, dy, dt, open_x=False, species=(),
-                 window=None):
-        self.g = _Grid(nx, ny, dx, dy, dt, 1 if open_x else 0)
+                 window=None, filter_j=False):
+        self.g = _Grid(nx, ny, dx, dy, dt, 1 if open_x else 0,
+                       1 if filter_j else 0)
         self.f = {k: np.zeros((ny, nx)) for k in FIELD_NAMES}
         self.fc = _Fields((_DP * 3)(*[_dp(self.f[k]) for k in FIELD_NAMES[0:3]]),
                           (_DP * 3)(*[_dp(self.f[k]) for k in FIELD_NAMES[3:6]]),
@@ -177,6 +180,10 @@ class Sim:
 
     def set_field(self, name, arr):
         self.f[name][...] = arr
+
+    def filter_current(self):
+        """Applies the compensated binomial filter to the J arrays."""
+        lib().orc_filter_current(C.byref(self.g), C.byref(self.fc))
 
     def laser(self, a0, omega0, w0, fwhm, x0, yc):
         lib().orc_laser(C.byref(self.g), C.byref(self.fc), a0, omega0, w0,

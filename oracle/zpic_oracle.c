@@ -316,6 +316,37 @@ void orc_push_deposit(const orc_grid *g, const orc_fields *f, orc_species *s,
     if (kin) *kin = ktot * g->dx * g->dy;
 }
 
+/* ---- Optional current filter (Sec. 2.2; compensated binomial, Sec. 4.1) ---- */
+
+/* One 3-point pass with weights (a, b, a) along x (dir 0) or y (dir 1). */
+static void filter_pass(const orc_grid *g, double *v, int dir, double a,
+                        double b) {
+    const long n = (long)g->nx * g->ny;
+    double *src = malloc(sizeof(double) * n);
+    memcpy(src, v, sizeof(double) * n);
+    for (int j = 0; j < g->ny; j++)
+        for (int i = 0; i < g->nx; i++) {
+            double lo, hi;
+            if (dir == 0) {
+                lo = fld(g, src, i - 1, j);
+                hi = fld(g, src, i + 1, j);
+            } else {
+                lo = fld(g, src, i, j - 1);
+                hi = fld(g, src, i, j + 1);
+            }
+            v[(long)j * g->nx + i] = a * lo + b * src[(long)j * g->nx + i] + a * hi;
+        }
+    free(src);
+}
+
+void orc_filter_current(const orc_grid *g, const orc_fields *f) {
+    for (int c = 0; c < 3; c++)
+        for (int dir = 0; dir < 2; dir++) {
+            filter_pass(g, f->j[c], dir, 0.25, 0.5);    /* binomial */
+            filter_pass(g, f->j[c], dir, -0.25, 1.5);   /* compensation */
+        }
+}
+
 /* ---- Stage 4: Yee FDTD field advance (Sec. 2.2) ---- */
 
 void orc_yee_b_half(const orc_grid *g, const orc_fields *f) {
@@ -475,6 +506,7 @@ int orc_step(const orc_grid *g, const orc_fields *f, int nspecies,
         orc_push_deposit(g, f, &sp[s], 1, nthreads, &kin);
         if (energy_out) energy_out[2 + s] = kin;
     }
+    if (g->filter_j) orc_filter_current(g, f);
     orc_yee_b_half(g, f);
     orc_yee_e(g, f);
     orc_yee_b_half(g, f);

@@ -43,6 +43,9 @@ typedef struct {
     int nx, ny;            /* cells */
     double dx, dy, dt;     /* cell size, time step */
     int open_x;            /* 0: periodic x; 1: open x (moving window) */
+    int filter_j;          /* 1: smooth J with the compensated binomial
+                              filter (orc_filter_current) before the field
+                              update */
 } orc_grid;
 
 typedef struct {
@@ -96,6 +99,15 @@ int orc_move_deposit(const orc_grid *g, const orc_fields *f, int *ix, int *iy,
  * is summed in thread order (the particle decomposition of Sec. 3.1). */
 void orc_push_deposit(const orc_grid *g, const orc_fields *f, orc_species *s,
                       int do_deposit, int nthreads, double *kin);
+
+/* Optional digital filter of the current (Sec. 2.2: a filter on J against
+ * short-wavelength noise; Sec. 4.1: the LWFA runs use a compensated
+ * binomial filter).  Per axis, x then y, and per component on its own
+ * grid: one binomial pass (1, 2, 1)/4, then one compensation pass
+ * (-1, 6, -1)/4, so a mode of wavenumber k is multiplied by
+ * (1 - sin^2(k/2)) (1 + sin^2(k/2)) = 1 - sin^4(k/2) per axis.  y is
+ * periodic; x is periodic, or open (values outside [0, nx) are zero). */
+void orc_filter_current(const orc_grid *g, const orc_fields *f);
 
 /* Stage 4: B -= (dt/2) curl E ; E += dt (curl B - J). */
 void orc_yee_b_half(const orc_grid *g, const orc_fields *f);

@@ -16,6 +16,11 @@ and momenta.  The workloads:
   linear density ramp of length 5 that starts at the box edge.
 * precision_study: 2048x2048 cells, dx=dy=0.1, dt=0.07, electrons and
   positrons 8x8 per cell each, u_th=0.1 (FP32 or FP64).
+* weibel: the paper's cloud-collision (Weibel) case, 512x512 cells,
+  electrons and positrons 16x16 per cell each, uniform over the box,
+  drifting in opposite directions along z (perpendicular to the plane);
+  drift 0.6, u_th=0.1, dx=dy=0.1, dt=0.07 (the paper gives grid and ppc
+  only).
 * batch_sweep: independent small simulations (see synthetic.plasma.
   batch_specs for how sizes, ppc and u_th are drawn).
 """
@@ -67,6 +72,14 @@ def precision_study(nx=2048, ny=2048, ppc=(8, 8), u_th=0.1, dt=0.07, d=0.1,
                     precision=Z.FP32, **kw):
     sps = [Z.species(-1.0, ppc, u_th=(u_th,) * 3),
            Z.species(1.0, ppc, u_th=(u_th,) * 3)]
+    return Z.config(nx, ny, (nx * d, ny * d), dt, sps, precision=precision,
+                    seed=kw.pop("seed", SEED), **kw)
+
+
+def weibel(nx=512, ny=512, ppc=(16, 16), u_fl=0.6, u_th=0.1, dt=0.07,
+           d=0.1, precision=Z.FP32, **kw):
+    sps = [Z.species(-1.0, ppc, u_th=(u_th,) * 3, u_fl=(0.0, 0.0, u_fl)),
+           Z.species(1.0, ppc, u_th=(u_th,) * 3, u_fl=(0.0, 0.0, -u_fl))]
     return Z.config(nx, ny, (nx * d, ny * d), dt, sps, precision=precision,
                     seed=kw.pop("seed", SEED), **kw)
 

@@ -8,7 +8,9 @@ FP64 oracle on the same seeded inputs:
 * the full-size uniform plasma (2048^2 cells, 536,870,912 particles): one
   step, checked on a sampled region the oracle recomputes from the
   regenerated initial load, plus exact particle counts;
-* the precision study: FP32 and FP64 forms against the oracle at step 20.
+* the precision study: FP32 and FP64 forms against the oracle at step 20;
+* the Weibel case (electrons and positrons counter-drifting along z at
+  16x16 particles per cell each, 512 per cell in all) on a small box.
 """
 import numpy as np
 import pytest
@@ -207,3 +209,33 @@ def test_precision_study_fp32_vs_fp64(nx):
         errs[prec] = (f, p)
     assert errs[Z.FP64][0] < 1e-9 and errs[Z.FP64][1] < 1e-9
     assert errs[Z.FP64][0] < errs[Z.FP32][0] / 100
+
+
+def test_weibel_counter_streaming_parity():
+    # 512 particles per cell: the heaviest deposit load per cell of the
+    # workloads (fixed-point current words take ~2000 adds per step here)
+    nx = ny = 32
+    cfg = W.weibel(nx, ny, track_ids=True, energy_every=5)
+    loads = [P.plasma_load(nx, ny, 16, 16, species=s, u_th=(0.1,) * 3,
+                           u_fl=(0.0, 0.0, 0.6 if s == 0 else -0.6))
+             for s in range(2)]
+    gpu = Z.Sim(cfg)
+    for s in range(2):
+        assert gpu.num_particles(s) == nx * ny * 256
+    orc = oracle_from_load(cfg, loads)
+    refs = [H.positions_by_id(sp.state()) for sp in orc.species]
+    gpu.step(10)
+    orc.step(10, nthreads=4)
+    H.compare_fields(gpu, orc, 1e-4)
+    for s in range(2):
+        H.compare_particles(gpu, orc, s, nx, ny, 1e-4, x_ref=refs[s])
+    # the counter-streaming currents along z: Jz dominates Jx, Jy
+    jz = np.linalg.norm(gpu.field("jz"))
+    assert jz > 3 * np.linalg.norm(gpu.field("jx"))
+    for (st, wE, wB, kin), (ost, owE, owB, okin) in zip(gpu.energy(),
+                                                         orc.history[4::5]):
+        assert st == ost
+        assert kin[0] == pytest.approx(okin[0], rel=1e-5)
+        assert kin[1] == pytest.approx(okin[1], rel=1e-5)
+        assert wB == pytest.approx(owB, rel=1e-3)
+
