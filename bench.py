@@ -56,8 +56,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=512,
                     help="cells per side of the oracle sample")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "clouds", "lwfa", "weibel", "batch",
-                             "precision"],
+                    choices=["uniform", "clouds", "lwfa", "lwfa_paper",
+                             "weibel", "batch", "precision"],
                     help="uniform (default): the large uniform plasma; the "
                     "others print one line for that workload")
     return ap.parse_args()
@@ -313,12 +313,18 @@ def other_workload(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    if args.workload in ("clouds", "lwfa", "weibel"):
+    if args.workload in ("clouds", "lwfa", "lwfa_paper", "weibel"):
         if args.workload == "clouds":
             cfg = W.clouds(energy_every=10)
             warm = args.warmup
             desc = ("collision of plasma clouds 1024x1024, e-/e+ 4x4 ppc in "
                     "two clouds drifting +-0.2, u_th 0.05, FP32")
+        elif args.workload == "lwfa_paper":
+            cfg = W.lwfa_paper(energy_every=10)
+            warm = max(args.warmup, 2000)   # let the plasma fill the window
+            desc = ("laser wakefield, the paper's form: 2000x512, 16 ppc "
+                    "(4x4 lattice) behind a ramp, compensated binomial "
+                    "current filter, moving window, FP32")
         elif args.workload == "weibel":
             cfg = W.weibel(energy_every=10)
             warm = args.warmup

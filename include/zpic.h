@@ -88,6 +88,12 @@ extern "C" {
 
 /* config flags */
 #define ZPIC_TRACK_IDS 1       /* keep a per-particle int32 id (parity)    */
+#define ZPIC_FILTER_J 2        /* smooth J before the field update with the
+                                  compensated binomial filter (Sec. 2.2
+                                  digital filter, Sec. 4.1 LWFA runs): per
+                                  axis one (1,2,1)/4 and one (-1,6,-1)/4
+                                  pass; the J getters then return the
+                                  filtered current */
 
 typedef struct {
     double q_over_m;    /* charge-to-mass ratio (electrons: -1)          */
@@ -126,7 +132,7 @@ typedef struct {
     int sim_index;              /* generator stream of this simulation    */
     int energy_every;           /* record energies every k steps; 0: off  */
     int tile_x, tile_y;         /* tile size in cells, 2..32; 0: 16       */
-    int flags;                  /* ZPIC_TRACK_IDS                         */
+    int flags;                  /* ZPIC_TRACK_IDS | ZPIC_FILTER_J         */
     double capacity_slack;      /* spare tile capacity fraction; 0: 0.25  */
 } zpic_config;
 

@@ -83,10 +83,12 @@ __global__ void __launch_bounds__(kThreads)
     const int lj = r / BW, li = r - lj * BW;
     sb[c][lj][li] = fld(S, S.B[cur][c], x0 - 1 + li, y0 - 1 + lj);
   }
+  // the current that drives E: this step's deposit, or its filtered copy
+  const R *const *jsrc = S.Jf[0] ? S.Jf : S.J[cur];
   for (int k = threadIdx.x; k < 3 * JH * JW; k += blockDim.x) {
     const int c = k / (JH * JW), r = k - c * (JH * JW);
     const int lj = r / JW, li = r - lj * JW;
-    sj[c][lj][li] = fld(S, S.J[cur][c], x0 + li, y0 + lj);
+    sj[c][lj][li] = fld(S, jsrc[c], x0 + li, y0 + lj);
   }
   __syncthreads();
 
@@ -168,6 +170,78 @@ __global__ void __launch_bounds__(kThreads)
     b2 = block_sum(b2, red);
     if (threadIdx.x == 0) S.part_fld[b + 1] = b2;
   }
+}
+
+// Compensated binomial filter of the current (optional; Sec. 2.2 digital
+// filter on J, Sec. 4.1 LWFA runs): per component and per axis, x then y,
+// one (1, 2, 1)/4 pass and one (-1, 6, -1)/4 pass.  One CTA per 32 x 8
+// block: J on [-2, 34) x [-2, 10) in shared memory, the two x passes on all
+// 12 rows, the two y passes on the block's rows; with an open x boundary
+// every pass reads zero outside [0, nx), as if each pass were a separate
+// sweep over the grid.  Writes Jf, which the Yee kernel then reads.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    filter_kernel(const SimDev<R> *__restrict__ sims,
+                  const int2 *__restrict__ items, BatchStatus *st) {
+  constexpr int X = kYeeX, Y = kYeeY;
+  constexpr int W = X + 4, H = Y + 4;
+  static_assert(X * Y == kThreads, "one thread per output cell");
+  __shared__ R a[H][W];       // J, then the compensated x pass
+  __shared__ R b[H][W];       // binomial x pass, then binomial y pass
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const int2 it = items[blockIdx.x];
+  const SimDev<R> &S = sims[it.x];
+  if (!S.Jf[0]) return;
+  const int x0 = (it.y % S.ybx) * X, y0 = (it.y / S.ybx) * Y;
+  const int cur = step & 1;
+  const bool open_x = S.open_x != 0;
+  const R q = R(0.25), h = R(0.5), c15 = R(1.5);
+  for (int c = 0; c < 3; ++c) {
+    for (int k = threadIdx.x; k < H * W; k += blockDim.x) {
+      const int lj = k / W, li = k - lj * W;
+      a[lj][li] = fld(S, S.J[cur][c], x0 - 2 + li, y0 - 2 + lj);
+    }
+    __syncthreads();
+    // x binomial on local columns 1..W-2 (global x0 - 1 .. x0 + X)
+    for (int k = threadIdx.x; k < H * (W - 2); k += blockDim.x) {
+      const int lj = k / (W - 2), li = 1 + k - lj * (W - 2);
+      const int gi = x0 - 2 + li;
+      const bool out = open_x && (gi < 0 || gi >= S.nx);
+      b[lj][li] = out ? R(0)
+                      : q * a[lj][li - 1] + h * a[lj][li] + q * a[lj][li + 1];
+    }
+    __syncthreads();
+    // x compensation on local columns 2..W-3 (the block's own columns)
+    for (int k = threadIdx.x; k < H * X; k += blockDim.x) {
+      const int lj = k / X, li = 2 + k - lj * X;
+      a[lj][li] = -q * b[lj][li - 1] + c15 * b[lj][li] - q * b[lj][li + 1];
+    }
+    __syncthreads();
+    // y binomial on local rows 1..H-2 (y is periodic: no edge rule)
+    for (int k = threadIdx.x; k < (H - 2) * X; k += blockDim.x) {
+      const int lj = 1 + k / X, li = 2 + k % X;
+      b[lj][li] = q * a[lj - 1][li] + h * a[lj][li] + q * a[lj + 1][li];
+    }
+    __syncthreads();
+    // y compensation on the block's own rows, written out
+    {
+      const int i = threadIdx.x % X, j = threadIdx.x / X;
+      const int gi = x0 + i, gj = y0 + j;
+      const int li = i + 2, lj = j + 2;
+      const R v = -q * b[lj - 1][li] + c15 * b[lj][li] - q * b[lj + 1][li];
+      if (gi < S.nx && gj < S.ny) S.Jf[c][(size_t)gj * S.ld + gi] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+cudaError_t launch_filter(const SimDev<R> *sims, const int2 *items,
+                          int n_items, BatchStatus *st, cudaStream_t stream) {
+  if (n_items == 0) return cudaSuccess;
+  filter_kernel<R><<<n_items, kThreads, 0, stream>>>(sims, items, st);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -338,6 +412,8 @@ cudaError_t launch_laser(const SimDev<R> *sim_dev, int nx, int ny,
 }
 
 #define ZP_INST(R)                                                          \
+  template cudaError_t launch_filter<R>(const SimDev<R> *, const int2 *,   \
+                                        int, BatchStatus *, cudaStream_t); \
   template cudaError_t launch_yee<R>(const SimDev<R> *, const int2 *, int, \
                                      BatchStatus *, cudaStream_t);          \
   template cudaError_t launch_end_step<R>(const SimDev<R> *, int,          \

@@ -743,35 +743,41 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
   T.red = red;
 
   // ---- stage 0: fields of the tile + one guard cell, coefficient form ----
+  // one cell per thread and pass, the six components inner (index
+  // arithmetic and boundary handling shared by the six loads)
   R *raw = reinterpret_cast<R *>(smem_raw + L.q);
-  for (int k = threadIdx.x; k < 6 * FP; k += blockDim.x) {
-    const int c = k / FP, r = k - c * FP;
+  for (int r = threadIdx.x; r < FP; r += blockDim.x) {
     const int lj = r / FW, li = r - lj * FW;
-    const R *src = c < 3 ? S.E[CUR][c] : S.B[CUR][c - 3];
     int gi = x0 - 1 + li;
     const int gj = wrap1(y0 - 1 + lj, ny);
-    R v = R(0);
-    if (open_x) {
-      if (gi >= 0 && gi < nx) v = src[(size_t)gj * ld + gi];
-    } else {
+    bool in = true;
+    if (open_x)
+      in = gi >= 0 && gi < nx;
+    else
       gi = wrap1(gi, nx);
-      v = src[(size_t)gj * ld + gi];
+    const size_t o = (size_t)gj * ld + (in ? gi : 0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const R *src = c < 3 ? S.E[CUR][c] : S.B[CUR][c - 3];
+      raw[c * FP + r] = in ? src[o] : R(0);
     }
-    raw[k] = v;
   }
   T.jt.zero(JP);
   __syncthreads();
-  for (int k = threadIdx.x; k < 6 * CP; k += blockDim.x) {
-    const int c = k / CP, r = k - c * CP;
+  for (int r = threadIdx.x; r < CP; r += blockDim.x) {
     const int cj = r / CW, ci = r - cj * CW;
-    const R *f = raw + c * FP + cj * FW + ci;
-    const R f00 = f[0], f10 = f[1], f01 = f[FW], f11 = f[FW + 1];
-    Coef4<R> v;
-    v.a = f00;
-    v.b = f10 - f00;
-    v.c = f01 - f00;
-    v.d = (f11 - f10) - v.c;
-    cf[k] = v;
+    const int b = cj * FW + ci;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const R *f = raw + c * FP + b;
+      const R f00 = f[0], f10 = f[1], f01 = f[FW], f11 = f[FW + 1];
+      Coef4<R> v;
+      v.a = f00;
+      v.b = f10 - f00;
+      v.c = f01 - f00;
+      v.d = (f11 - f10) - v.c;
+      cf[c * CP + r] = v;
+    }
   }
   // (the species loop's barrier separates these reads of the staging area
   // from the queue writes)
@@ -797,10 +803,7 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
   __syncthreads();
 
   // ---- stage 3b: fold the tile's current (with guards) into global J ----
-  for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) {
-    const int c = k / JP, r = k - c * JP;
-    double v;
-    if (!T.jt.value(c, r, JW, JP, v)) continue;
+  for (int r = threadIdx.x; r < JP; r += blockDim.x) {
     const int lj = r / JW, li = r - lj * JW;
     int gi = x0 - 1 + li;
     const int gj = wrap1(y0 - 1 + lj, ny);
@@ -809,7 +812,13 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
     } else {
       gi = wrap1(gi, nx);
     }
-    atomicAdd(S.J[CUR][c] + (size_t)gj * ld + gi, (R)(v * S.jscale[c]));
+    const size_t o = (size_t)gj * ld + gi;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v;
+      if (T.jt.value(c, r, JW, JP, v))
+        atomicAdd(S.J[CUR][c] + o, (R)(v * S.jscale[c]));
+    }
   }
 }
 
@@ -831,6 +840,18 @@ __global__ void __launch_bounds__(kPT, sizeof(R) == 4 ? kPushCtasF32 : 2)
   if (frozen(st, step)) return;
   const int2 it = items[blockIdx.x];
   const SimDev<R> &S = kBatch ? sims[it.x] : one;
+  // a tile without particles deposits nothing and loses nothing: it only
+  // reports empty outboxes (and zero kinetic energy on energy steps)
+  int n_all = 0;
+  for (int s = 0; s < S.nsp; ++s) n_all += S.sp[s].cnt[it.y];
+  if (n_all == 0) {
+    if (threadIdx.x < S.nsp) {
+      S.sp[threadIdx.x].ob_cnt[it.y] = 0;
+      if (S.energy_every > 0 && ((step + 1) % S.energy_every) == 0)
+        S.part_kin[(size_t)it.y * kMaxSpecies + threadIdx.x] = 0.0;
+    }
+    return;
+  }
   if (step & 1)
     push_tile<R, kBatch, TXC, TYC, 1>(S, it.x, it.y, step, st, ovf, smem_raw,
                                       s_slots, red);

@@ -124,6 +124,8 @@ int validate(const zpic_config *c) {
     return fail(ZPIC_EINVAL, "tile sizes must be 0 or in [2, 32]");
   if (c->capacity_slack < 0 || c->capacity_slack > 16)
     return fail(ZPIC_EINVAL, "capacity_slack out of range");
+  if (c->flags & ~(ZPIC_TRACK_IDS | ZPIC_FILTER_J))
+    return fail(ZPIC_EINVAL, "unknown flags");
   const double dx = c->box_x / c->nx, dy = c->box_y / c->ny;
   const double cfl = 1.0 / std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy));
   if (!(c->dt < cfl)) return fail(ZPIC_ECFL, "dt violates the Courant limit");
@@ -367,7 +369,8 @@ class Batch : public BatchBase {
     if (which < 6)
       src = which < 3 ? S.dev.E[step & 1][which] : S.dev.B[step & 1][which - 3];
     else
-      src = S.dev.J[(step + 1) & 1][which - 6];  // last step's current
+      src = S.dev.Jf[0] ? S.dev.Jf[which - 6]     // the filtered current
+                        : S.dev.J[(step + 1) & 1][which - 6];  // last step's
     const bool same = want_f64 == (sizeof(R) == 8);
     if (same) {
       ZP_CU(cudaMemcpy2DAsync(dst, S.nx * sizeof(R), src, S.ld * sizeof(R),
@@ -688,7 +691,8 @@ class Batch : public BatchBase {
     S.ybx = (S.nx + kYeeX - 1) / kYeeX;
     S.yby = (S.ny + kYeeY - 1) / kYeeY;
     const size_t plane = (size_t)S.ny * S.ld;
-    if (!dalloc(S.fields, 18 * plane * sizeof(R)))
+    const bool filter = (c.flags & ZPIC_FILTER_J) != 0;
+    if (!dalloc(S.fields, (filter ? 21 : 18) * plane * sizeof(R)))
       return fail(ZPIC_ENOMEM, "fields");
     ZP_CU(cudaMemsetAsync(S.fields.p, 0, S.fields.bytes, stream_));
     R *f = (R *)S.fields.p;
@@ -720,6 +724,8 @@ class Batch : public BatchBase {
         D.B[a][c3] = f + (size_t)(a * 9 + 3 + c3) * plane;
         D.J[a][c3] = f + (size_t)(a * 9 + 6 + c3) * plane;
       }
+    for (int c3 = 0; c3 < 3; ++c3)
+      D.Jf[c3] = filter ? f + (size_t)(18 + c3) * plane : nullptr;
     if (!dalloc(S.part_kin, sizeof(double) * S.ntiles * kMaxSpecies) ||
         !dalloc(S.part_fld, sizeof(double) * 2 * S.ybx * S.yby))
       return fail(ZPIC_ENOMEM, "partials");
@@ -1189,6 +1195,15 @@ class Batch : public BatchBase {
   }
   BatchStatus *dst() const { return (BatchStatus *)st_mem_.p; }
 
+  // the kernels of one step, in order (the filter only when some
+  // simulation of the batch filters its current)
+  std::vector<int> stages() const {
+    bool filter = false;
+    for (const auto &S : sims_) filter = filter || S.dev.Jf[0] != nullptr;
+    if (filter) return {0, 4, 1, 2, 3};
+    return {0, 1, 2, 3};
+  }
+
   cudaError_t launch_stage(int k) {
     switch (k) {
       case 0:
@@ -1203,12 +1218,16 @@ class Batch : public BatchBase {
       case 2:
         return launch_migrate<R>(dsims(), (const int2 *)items_.p, n_items_,
                                  dst(), ovf_, stream_);
-      default:
+      case 3:
         return launch_end_step<R>(dsims(), n_sims, dst(), stream_);
+      default:
+        return launch_filter<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
+                                dst(), stream_);
     }
   }
   static const char *stage_name(int k) {
-    static const char *names[4] = {"push_deposit", "yee", "migrate", "end_step"};
+    static const char *names[5] = {"push_deposit", "yee", "migrate",
+                                   "end_step", "filter_current"};
     return names[k];
   }
 
@@ -1216,20 +1235,23 @@ class Batch : public BatchBase {
     if (n == 0) return ZPIC_OK;
     if (profiling_) {
       ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_, ring_wide()));
-      if (timers_.empty())
-        for (int k = 0; k < 4; ++k) {
+      const std::vector<int> order = stages();
+      if (timers_.size() != order.size()) {
+        timers_.clear();
+        for (int k : order) {
           timers_.emplace_back();
           timers_.back().name = stage_name(k);
         }
+      }
       for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 4; ++k) {
+        for (size_t t = 0; t < order.size(); ++t) {
           cudaEvent_t a, b;
           ZP_CU(cudaEventCreate(&a));
           ZP_CU(cudaEventCreate(&b));
           ZP_CU(cudaEventRecord(a, stream_));
-          ZP_CU(launch_stage(k));
+          ZP_CU(launch_stage(order[t]));
           ZP_CU(cudaEventRecord(b, stream_));
-          timers_[k].ev.push_back({a, b});
+          timers_[t].ev.push_back({a, b});
         }
       return ZPIC_OK;
     }
@@ -1248,7 +1270,8 @@ class Batch : public BatchBase {
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = launch_stage(k);
+      for (int k : stages())
+        if (e == cudaSuccess) e = launch_stage(k);
       cudaError_t e2 = cudaStreamEndCapture(cs, &g);
       if (e == cudaSuccess) e = e2;
     }

@@ -8,7 +8,8 @@
 // HBM layout per simulation (R = float or double):
 //   fields: E[2][3], B[2][3], J[2][3] arrays of ny rows x ld (ld = nx padded
 //           to 128 bytes); copy (step & 1) is current, the Yee kernel
-//           writes copy (step & 1) ^ 1 (ping-pong, no halo races);
+//           writes copy (step & 1) ^ 1 (ping-pong, no halo races); with the
+//           current filter on, 3 more arrays Jf hold the filtered J;
 //   particles, per species: SoA arrays cell (uint16, cell within the tile),
 //           x, y, ux, uy, uz (R), optional w (R) and id (int32), one segment per
 //           tile [off[t], off[t] + cap[t]) of which cnt[t] are live; two
@@ -94,6 +95,7 @@ struct SimDev {
   R dt_dx, dt_dy;              // dt/dx, dt/dy (cells per unit velocity)
   double dx_d, dy_d, dt_d;     // double values (window schedule, setup)
   R *E[2][3], *B[2][3], *J[2][3];
+  R *Jf[3];                    // filtered current (null: no filter)
   // FP32 tiles accumulate J exactly in two-word fixed point with 2^-30 units
   // of Uq dx/dt, Uq dy/dt, Uq (Uq = max |q0| x max weight, so one segment
   // contributes at most one unit); jscale converts a tile sum to J.

@@ -31,6 +31,12 @@ cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const OverflowDev<R> &ovf,
                                 cudaStream_t stream);
 
+// Optional current filter over all (sim, yee block) items: Jf = compensated
+// binomial filter of this step's J (simulations without Jf are skipped).
+template <typename R>
+cudaError_t launch_filter(const SimDev<R> *sims, const int2 *items,
+                          int n_items, BatchStatus *st, cudaStream_t stream);
+
 // Stage 4 (B half, E, B half) over all (sim, yee block) items; writes the
 // other field copy (shifted one cell when the window moves), zeroes the
 // other J copy, field-energy partials on energy steps.

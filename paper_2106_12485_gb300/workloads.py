@@ -14,6 +14,9 @@ and momenta.  The workloads:
   periodic y, Gaussian laser a0=2, omega0=10, waist 4, FWHM 2 centred
   3 FWHM inside the right edge; cold electrons on a 2x2 lattice behind a
   linear density ramp of length 5 that starts at the box edge.
+* lwfa_paper: the paper's own LWFA shape (Sec. 4.1): 2000x512 cells,
+  16 particles per cell (4x4 lattice), compensated binomial current
+  filter; cell size, time step and laser as in lwfa.
 * precision_study: 2048x2048 cells, dx=dy=0.1, dt=0.07, electrons and
   positrons 8x8 per cell each, u_th=0.1 (FP32 or FP64).
 * weibel: the paper's cloud-collision (Weibel) case, 512x512 cells,
@@ -66,6 +69,10 @@ def lwfa(nx=4096, ny=512, dx=0.02, dy=0.2, dt=0.019, ppc=(2, 2),
     return Z.config(nx, ny, (Lx, Ly), dt, sps, precision=precision,
                     bc_x=Z.BC_OPEN, moving_window=True, laser=laser,
                     seed=kw.pop("seed", SEED), **kw)
+
+
+def lwfa_paper(nx=2000, ny=512, ppc=(4, 4), **kw):
+    return lwfa(nx=nx, ny=ny, ppc=ppc, filter_j=kw.pop("filter_j", True), **kw)
 
 
 def precision_study(nx=2048, ny=2048, ppc=(8, 8), u_th=0.1, dt=0.07, d=0.1,

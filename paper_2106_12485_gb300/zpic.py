@@ -24,6 +24,7 @@ FIELD_IDS = {"ex": EX, "ey": EY, "ez": EZ, "bx": BX, "by": BY, "bz": BZ,
              "jx": JX, "jy": JY, "jz": JZ}
 PROFILE_NONE, PROFILE_UNIFORM, PROFILE_SLAB, PROFILE_RAMP = 0, 1, 2, 3
 TRACK_IDS = 1
+FILTER_J = 2
 
 
 class zpic_species(C.Structure):
@@ -178,7 +179,7 @@ def species(q_over_m=-1.0, ppc=(4, 4), u_th=(0.0, 0.0, 0.0),
 def config(nx, ny, box, dt, species_list=(), precision=FP32,
            bc_x=BC_PERIODIC, moving_window=False, laser=None,
            seed=2106012485, sim_index=0, energy_every=0, tile=(0, 0),
-           track_ids=False, capacity_slack=0.0):
+           track_ids=False, capacity_slack=0.0, filter_j=False):
     c = zpic_config()
     c.nx, c.ny = nx, ny
     c.box_x, c.box_y = box
@@ -197,7 +198,7 @@ def config(nx, ny, box, dt, species_list=(), precision=FP32,
     c.sim_index = sim_index
     c.energy_every = energy_every
     c.tile_x, c.tile_y = tile
-    c.flags = TRACK_IDS if track_ids else 0
+    c.flags = (TRACK_IDS if track_ids else 0) | (FILTER_J if filter_j else 0)
     c.capacity_slack = capacity_slack
     return c
 

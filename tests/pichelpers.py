@@ -39,7 +39,8 @@ def make_pair(cfg, loads, fields=None, window=None, cap_extra=0):
                                       cap=len(ld["ix"]) + cap_extra))
     dx, dy = cfg.box_x / cfg.nx, cfg.box_y / cfg.ny
     orc = O.Sim(cfg.nx, cfg.ny, dx, dy, cfg.dt, open_x=bool(cfg.bc_x),
-                species=species, window=window)
+                species=species, window=window,
+                filter_j=bool(cfg.flags & Z.FILTER_J))
     if fields:
         for k, v in fields.items():
             gpu.set_field(k, v)

@@ -32,7 +32,8 @@ def oracle_from_load(cfg, loads, window=None, cap_extra=0):
                                         cap=len(ld["ix"]) + cap_extra))
     dx, dy = cfg.box_x / cfg.nx, cfg.box_y / cfg.ny
     return O.Sim(cfg.nx, cfg.ny, dx, dy, cfg.dt, open_x=bool(cfg.bc_x),
-                 species=species, window=window)
+                 species=species, window=window,
+                 filter_j=bool(cfg.flags & Z.FILTER_J))
 
 
 def empty_load():
@@ -42,16 +43,16 @@ def empty_load():
             "id": np.zeros(0, np.int32)}
 
 
-def lwfa_pair(nx, ny, steps, precision):
+def lwfa_pair(nx, ny, steps, precision, ppc=(2, 2), filter_j=False):
     cfg = W.lwfa(nx=nx, ny=ny, track_ids=True, energy_every=10,
-                 precision=precision)
+                 precision=precision, ppc=ppc, filter_j=filter_j)
     Lx = nx * 0.02
     gpu = Z.Sim(cfg)
-    window = {"species": [{"ppc_x": 2, "ppc_y": 2, "ramp_x0": Lx,
+    window = {"species": [{"ppc_x": ppc[0], "ppc_y": ppc[1], "ramp_x0": Lx,
                            "ramp_len": 5.0, "n0": 1.0,
-                           "id_base": nx * ny * 4}]}
+                           "id_base": nx * ny * ppc[0] * ppc[1]}]}
     orc = oracle_from_load(cfg, [empty_load()], window=window,
-                           cap_extra=steps * ny * 4 + 16)
+                           cap_extra=steps * ny * ppc[0] * ppc[1] + 16)
     l = cfg.laser
     orc.laser(l.a0, l.omega0, l.w0, l.fwhm, l.x0, l.y_center)
     return gpu, orc
@@ -95,6 +96,20 @@ def test_lwfa_window_laser_injection_parity_fp32():
     nx, ny, steps = 512, 32, 300
     gpu, orc = lwfa_pair(nx, ny, steps, Z.FP32)
     H.compare_fields(gpu, orc, 1e-6, names=H.FIELDS[:6])    # laser init
+    check_lwfa(gpu, orc, nx, ny, steps, 1e-4, 1e-3)
+
+
+def test_lwfa_paper_shape_with_current_filter_fp64():
+    # the paper's LWFA form (16 ppc, compensated binomial current filter) on
+    # a short box, FP64 against the oracle at rounding level
+    nx, ny, steps = 384, 32, 400
+    gpu, orc = lwfa_pair(nx, ny, steps, Z.FP64, ppc=(4, 4), filter_j=True)
+    check_lwfa(gpu, orc, nx, ny, steps, 1e-10, 1e-10)
+
+
+def test_lwfa_paper_shape_with_current_filter_fp32():
+    nx, ny, steps = 384, 32, 250
+    gpu, orc = lwfa_pair(nx, ny, steps, Z.FP32, ppc=(4, 4), filter_j=True)
     check_lwfa(gpu, orc, nx, ny, steps, 1e-4, 1e-3)
 
 
