@@ -175,6 +175,21 @@ typedef struct {
     size_t device_bytes;        /* device memory held                     */
 } zpic_info;
 
+/* Run state beyond fields and particles, for checkpoint / restart. */
+typedef struct {
+    int64_t step;               /* completed steps                        */
+    int32_t n_shift;            /* moving-window shifts done              */
+    int32_t reserved;
+    int64_t removed[ZPIC_MAX_SPECIES];  /* particles removed at open edges */
+} zpic_state;
+
+/* Phase-space quantities for zpic_phasespace. */
+#define ZPIC_PS_X 0    /* global x position in cells, ix + x */
+#define ZPIC_PS_Y 1    /* global y position in cells, iy + y */
+#define ZPIC_PS_UX 2
+#define ZPIC_PS_UY 3
+#define ZPIC_PS_UZ 4
+
 typedef struct zpic_sim zpic_sim;
 typedef struct zpic_batch zpic_batch;
 
@@ -277,6 +292,33 @@ int zpic_get_info(zpic_sim *sim, zpic_info *info);
  * the order zpic_get_particles writes them. */
 int zpic_get_tile_counts(zpic_sim *sim, int species, int32_t *dst,
                          size_t cap);
+
+/* Checkpoint / restart.  A run is fully described by its configuration,
+ * the fields E and B (zpic_get_fields_f64 / zpic_set_fields_f64), the
+ * particles of every species with their ids (zpic_get_particles /
+ * zpic_set_particles) and this state.  zpic_get_state fills *out (after a
+ * sync).  zpic_set_state restores it on a handle created from the same
+ * configuration, before or after the fields and particles are set (the
+ * current field and particle copies follow the step parity); the energy
+ * history restarts empty.  Errors: ZPIC_EINVAL for NULL, a negative step
+ * or n_shift, a removed count < 0, or a view into a batch of more than one
+ * simulation (the step counter is shared by the batch). */
+int zpic_get_state(zpic_sim *sim, zpic_state *out);
+int zpic_set_state(zpic_sim *sim, const zpic_state *in);
+
+/* Phase-space report (the paper's field / phase-space reports, Sec. 4.1)
+ * computed on the device: a 2D histogram of quantities qx, qy (ZPIC_PS_*)
+ * of one species, nbx x nby bins over [range[0], range[1]) x
+ * [range[2], range[3]), every particle adding its charge magnitude
+ * |q0| w (a charge density per bin).  The bin of a value v on an axis with
+ * bounds lo, hi and nb bins is floor((v - lo) * (nb / (hi - lo))),
+ * evaluated in double; particles outside either range are not counted.
+ * dst: caller-owned, nby rows of nbx doubles (cap >= nbx * nby, else
+ * ZPIC_ECAP).  Errors: ZPIC_EINVAL for a bad species, quantity, bin count
+ * (1..4096 per axis) or range (hi > lo, finite). */
+int zpic_phasespace(zpic_sim *sim, int species, int qx, int qy,
+                    const double range[4], int nbx, int nby, double *dst,
+                    size_t cap);
 
 /* Kernel timing: when enabled, zpic_step launches kernels one by one and
  * records a CUDA event pair around each launch on the handle's stream.

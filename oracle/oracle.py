@@ -236,3 +236,31 @@ def boris(qm, dt, E, B, u):
     ua = (C.c_double * 3)(*u)
     lib().orc_boris(qm, dt, Ea, Ba, ua)
     return np.array(ua[:])
+
+
+def phasespace(state, q0, qx, qy, range_, bins):
+    """Phase-space density of one species (the field / phase-space reports of
+    Sec. 4.1): every particle adds |q0| w to the bin (bx, by) of quantities
+    qx, qy ("x", "y": global position ix + x, iy + y in cells; "ux", "uy",
+    "uz").  On an axis with bounds lo, hi and nb bins, the bin of v is
+    floor((v - lo) * (nb / (hi - lo))) in double precision, and particles
+    whose bin falls outside [0, nb) on either axis are not counted.
+    Returns an (nby, nbx) array."""
+    vals = {"x": state["ix"] + np.asarray(state["x"], np.float64),
+            "y": state["iy"] + np.asarray(state["y"], np.float64),
+            "ux": np.asarray(state["ux"], np.float64),
+            "uy": np.asarray(state["uy"], np.float64),
+            "uz": np.asarray(state["uz"], np.float64)}
+    nbx, nby = bins
+    xlo, xhi, ylo, yhi = (float(v) for v in range_)
+    tx = (vals[qx] - xlo) * (nbx / (xhi - xlo))
+    ty = (vals[qy] - ylo) * (nby / (yhi - ylo))
+    keep = (tx >= 0) & (tx < nbx) & (ty >= 0) & (ty < nby)
+    w = state.get("w")
+    w = np.ones(len(tx)) if w is None else np.asarray(w, np.float64)
+    hist = np.zeros((nby, nbx))
+    np.add.at(hist, (np.floor(ty[keep]).astype(np.int64),
+                     np.floor(tx[keep]).astype(np.int64)),
+              abs(q0) * w[keep])
+    return hist
+

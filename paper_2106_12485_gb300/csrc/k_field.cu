@@ -281,10 +281,10 @@ __global__ void __launch_bounds__(kThreads)
     e = block_sum(e, red);
     b = block_sum(b, red);
     if (threadIdx.x == 0) {
-      const int rec = (step + 1) / S.energy_every - 1;
+      const int rec = (step + 1) / S.energy_every - 1 - S.hist_skip;
       const double area = S.dx_d * S.dy_d;
       bool bad = !isfinite(e) || !isfinite(b);
-      if (rec < S.hist_cap) {
+      if (rec >= 0 && rec < S.hist_cap) {
         zpic_energy_rec &r = S.hist[rec];
         r.step = step + 1;
         r.n_species = S.nsp;

@@ -386,6 +386,59 @@ cudaError_t launch_compact(SpeciesDev<R> sp, int b, int tx, int ty, int ntx,
   return cudaGetLastError();
 }
 
+// Phase-space density of one species (diagnostic report): every particle
+// adds |q0| w to the bin (bx, by) of two of its quantities (global position
+// in cells ix + x, iy + y, or a momentum component), b = floor((v - lo) *
+// nb / (hi - lo)) evaluated in double, kept when 0 <= b < nb.  One CTA per
+// tile, double atomics into hist (nby rows of nbx).
+template <typename R>
+__device__ __forceinline__ double ps_value(int q, int gx, int gy, R x, R y,
+                                           R ux, R uy, R uz) {
+  switch (q) {
+    case ZPIC_PS_X: return (double)gx + (double)x;
+    case ZPIC_PS_Y: return (double)gy + (double)y;
+    case ZPIC_PS_UX: return (double)ux;
+    case ZPIC_PS_UY: return (double)uy;
+    default: return (double)uz;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    phasespace_kernel(SpeciesDev<R> P, int b, int tx, int ty, int ntx,
+                      PhaseSpaceSpec ps, double *hist) {
+  const Planes<R> &I = P.buf[b];
+  const int t = blockIdx.x;
+  const int x0 = (t % ntx) * tx, y0 = (t / ntx) * ty;
+  const int n = P.cnt[t];
+  const size_t src = (size_t)P.off[t];
+  const double q0 = ps.q0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int c = I.cell[src + k];
+    const int gx = x0 + (c & 255), gy = y0 + (c >> 8);
+    const R x = I.x[src + k], y = I.y[src + k];
+    const R ux = I.ux[src + k], uy = I.uy[src + k], uz = I.uz[src + k];
+    const double tx_ = (ps_value(ps.qx, gx, gy, x, y, ux, uy, uz) - ps.lo[0]) *
+                       ps.scale[0];
+    const double ty_ = (ps_value(ps.qy, gx, gy, x, y, ux, uy, uz) - ps.lo[1]) *
+                       ps.scale[1];
+    if (!(tx_ >= 0.0 && tx_ < (double)ps.nbx)) continue;
+    if (!(ty_ >= 0.0 && ty_ < (double)ps.nby)) continue;
+    const double w = I.w ? (double)I.w[src + k] : 1.0;
+    atomicAdd(hist + (size_t)(int)ty_ * ps.nbx + (int)tx_, q0 * w);
+  }
+}
+
+template <typename R>
+cudaError_t launch_phasespace(SpeciesDev<R> sp, int b, int tx, int ty, int ntx,
+                              int ntiles, PhaseSpaceSpec ps, double *hist,
+                              cudaStream_t stream) {
+  if (ntiles == 0) return cudaSuccess;
+  phasespace_kernel<R><<<ntiles, kThreads, 0, stream>>>(sp, b, tx, ty, ntx, ps,
+                                                        hist);
+  return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void take_overflow_kernel(OverflowDev<R> ovf, int n_entries,
                                      int sim, int species, Staging<R> out,
@@ -434,6 +487,9 @@ cudaError_t launch_take_overflow(OverflowDev<R> ovf, int n_entries, int sim,
   template cudaError_t launch_compact<R>(SpeciesDev<R>, int, int, int, int,   \
                                          int, int, const long long *,         \
                                          Staging<R>, cudaStream_t);           \
+  template cudaError_t launch_phasespace<R>(SpeciesDev<R>, int, int, int, int, \
+                                            int, PhaseSpaceSpec, double *,    \
+                                            cudaStream_t);                    \
   template cudaError_t launch_take_overflow<R>(OverflowDev<R>, int, int, int, \
                                                Staging<R>, long long, int *,  \
                                                cudaStream_t);

@@ -208,6 +208,10 @@ struct BatchBase {
   virtual int info(int sim, zpic_info *out) = 0;
   virtual int field_energy(int sim, double *wE, double *wB) = 0;
   virtual int tile_counts(int sim, int sp, int32_t *dst, size_t cap) = 0;
+  virtual int get_state(int sim, zpic_state *out) = 0;
+  virtual int set_state(int sim, const zpic_state *in) = 0;
+  virtual int phasespace(int sim, int sp, int qx, int qy, const double *range,
+                         int nbx, int nby, double *dst, size_t cap) = 0;
   virtual int profile_enable(int en) = 0;
   virtual int profile_read(char *names, size_t name_len, double *ms,
                            int32_t *launches, int cap, int *n, int reset) = 0;
@@ -608,6 +612,103 @@ class Batch : public BatchBase {
     return ZPIC_OK;
   }
 
+  // ---- checkpoint / restart --------------------------------------------------
+
+  int get_state(int si, zpic_state *o) override {
+    if (!o) return fail(ZPIC_EINVAL, "NULL state");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    int small[2 + kMaxSpecies];
+    ZP_CU(cudaMemcpy(small + 1, S.dev.n_shift, sizeof(int) * (1 + kMaxSpecies),
+                     cudaMemcpyDeviceToHost));
+    std::memset(o, 0, sizeof(*o));
+    o->step = h_st_->step;
+    o->n_shift = small[1];
+    for (int s = 0; s < kMaxSpecies; ++s) o->removed[s] = small[2 + s];
+    return ZPIC_OK;
+  }
+
+  int set_state(int si, const zpic_state *in) override {
+    if (!in) return fail(ZPIC_EINVAL, "NULL state");
+    if (n_sims != 1)
+      return fail(ZPIC_EINVAL, "set_state on a batch of several simulations");
+    if (in->step < 0 || in->step > INT_MAX / 2 || in->n_shift < 0)
+      return fail(ZPIC_EINVAL, "step or n_shift out of range");
+    for (int s = 0; s < kMaxSpecies; ++s)
+      if (in->removed[s] < 0 || in->removed[s] > INT_MAX)
+        return fail(ZPIC_EINVAL, "removed count out of range");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    const int old_step = h_st_->step, new_step = (int)in->step;
+    if ((old_step ^ new_step) & 1) {
+      // the current copies are those of the step parity: swap the roles of
+      // the two field copies and of the two particle stores (J of the
+      // current copy stays zero, as a step expects)
+      for (int c = 0; c < 3; ++c) {
+        std::swap(S.dev.E[0][c], S.dev.E[1][c]);
+        std::swap(S.dev.B[0][c], S.dev.B[1][c]);
+        std::swap(S.dev.J[0][c], S.dev.J[1][c]);
+      }
+      for (int s = 0; s < (int)S.sp.size(); ++s) {
+        std::swap(S.dev.sp[s].buf[0], S.dev.sp[s].buf[1]);
+        std::swap(S.sp[s].store[0], S.sp[s].store[1]);
+      }
+    }
+    int small[2 + kMaxSpecies] = {0};
+    small[1] = in->n_shift;
+    for (int s = 0; s < kMaxSpecies; ++s) small[2 + s] = (int)in->removed[s];
+    ZP_CU(cudaMemcpyAsync(S.dev.hist_n, small, sizeof(int) * (2 + kMaxSpecies),
+                          cudaMemcpyHostToDevice, stream_));
+    S.dev.hist_skip = S.cfg.energy_every > 0 ? new_step / S.cfg.energy_every : 0;
+    h_st_->step = new_step;
+    target_ = new_step;
+    ZP_TRY(reset_status());
+    ZP_TRY(upload_descriptors());
+    return ZPIC_OK;
+  }
+
+  // ---- phase-space report ---------------------------------------------------
+
+  int phasespace(int si, int s, int qx, int qy, const double *range, int nbx,
+                 int nby, double *dst, size_t cap) override {
+    if (!range || !dst) return fail(ZPIC_EINVAL, "NULL range or buffer");
+    if (qx < ZPIC_PS_X || qx > ZPIC_PS_UZ || qy < ZPIC_PS_X || qy > ZPIC_PS_UZ)
+      return fail(ZPIC_EINVAL, "bad phase-space quantity");
+    if (nbx < 1 || nby < 1 || nbx > 4096 || nby > 4096)
+      return fail(ZPIC_EINVAL, "bin counts must be in [1, 4096]");
+    for (int k = 0; k < 4; ++k)
+      if (!std::isfinite(range[k])) return fail(ZPIC_EINVAL, "range not finite");
+    if (!(range[1] > range[0]) || !(range[3] > range[2]))
+      return fail(ZPIC_EINVAL, "empty range");
+    if (cap < (size_t)nbx * nby) return fail(ZPIC_ECAP, "histogram buffer too small");
+    ZP_TRY(sync());
+    SimHost<R> &S = sims_[si];
+    if (s < 0 || s >= (int)S.sp.size()) return fail(ZPIC_EINVAL, "species");
+    const size_t bytes = sizeof(double) * (size_t)nbx * nby;
+    DevMem h;
+    if (!dalloc(h, bytes)) return fail(ZPIC_ENOMEM, "histogram");
+    PhaseSpaceSpec ps;
+    ps.qx = qx;
+    ps.qy = qy;
+    ps.nbx = nbx;
+    ps.nby = nby;
+    ps.lo[0] = range[0];
+    ps.lo[1] = range[2];
+    ps.scale[0] = (double)nbx / (range[1] - range[0]);
+    ps.scale[1] = (double)nby / (range[3] - range[2]);
+    ps.q0 = std::fabs(S.sp[s].q0);
+    cudaError_t e = cudaMemsetAsync(h.p, 0, bytes, stream_);
+    if (e == cudaSuccess)
+      e = launch_phasespace<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty, S.ntx,
+                               S.ntiles, ps, (double *)h.p, stream_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, h.p, bytes, cudaMemcpyDeviceToHost, stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    dfree(h);
+    if (e != cudaSuccess) return cuda_fail(e, "phase space");
+    return ZPIC_OK;
+  }
+
   int tile_counts(int si, int s, int32_t *dst, size_t cap) override {
     ZP_TRY(sync());
     SimHost<R> &S = sims_[si];
@@ -736,8 +837,10 @@ class Batch : public BatchBase {
     S.hist_cap = c.energy_every > 0 ? 4096 : 1;
     if (!dalloc(S.hist, sizeof(zpic_energy_rec) * S.hist_cap))
       return fail(ZPIC_ENOMEM, "history");
+    ZP_CU(cudaMemsetAsync(S.hist.p, 0, S.hist.bytes, stream_));
     D.hist = (zpic_energy_rec *)S.hist.p;
     D.hist_cap = S.hist_cap;
+    D.hist_skip = 0;
     if (!dalloc(S.energy_rows, sizeof(double) * (2 * (size_t)S.ny + 2)))
       return fail(ZPIC_ENOMEM, "energy scratch");
     if (!dalloc(S.small, sizeof(int) * (2 + kMaxSpecies)))
@@ -1474,6 +1577,23 @@ int zpic_get_info(zpic_sim *sim, zpic_info *info) {
 int zpic_get_tile_counts(zpic_sim *sim, int species, int32_t *dst, size_t cap) {
   ZP_SIM(sim);
   return B->tile_counts(I, species, dst, cap);
+}
+
+int zpic_get_state(zpic_sim *sim, zpic_state *out) {
+  ZP_SIM(sim);
+  return B->get_state(I, out);
+}
+
+int zpic_set_state(zpic_sim *sim, const zpic_state *in) {
+  ZP_SIM(sim);
+  return B->set_state(I, in);
+}
+
+int zpic_phasespace(zpic_sim *sim, int species, int qx, int qy,
+                    const double range[4], int nbx, int nby, double *dst,
+                    size_t cap) {
+  ZP_SIM(sim);
+  return B->phasespace(I, species, qx, qy, range, nbx, nby, dst, cap);
 }
 
 int zpic_profile_enable(zpic_sim *sim, int enable) {

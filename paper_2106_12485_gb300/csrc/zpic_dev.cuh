@@ -104,6 +104,8 @@ struct SimDev {
   double *part_fld;            // [ybx*yby][2] field-energy partials
   zpic_energy_rec *hist;       // energy history
   int hist_cap;
+  int hist_skip;               // records before the first one kept (a run
+                               // restored at step s keeps those after s)
   int *hist_n;                 // records written
   int *n_shift;                // window shifts done
   int *removed;                // [kMaxSpecies] particles removed at edges

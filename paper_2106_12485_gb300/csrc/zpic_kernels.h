@@ -114,6 +114,18 @@ cudaError_t launch_bin_scatter(Staging<R> in, long long n,
 // compacts tiles [tile0, tile0 + ntiles) of store copy `buf` into a
 // contiguous staging copy, tile tile0 + k from dst_off[k] on (global cells
 // rebuilt from the tile index and the local cell)
+// Phase-space histogram of one species: quantities qx, qy (ZPIC_PS_*),
+// bins over [lo, lo + nb / scale) per axis.
+struct PhaseSpaceSpec {
+  int qx, qy, nbx, nby;
+  double lo[2], scale[2];
+  double q0;  // |charge| of a weight-1 particle (double, from the host)
+};
+template <typename R>
+cudaError_t launch_phasespace(SpeciesDev<R> sp_host_copy, int buf, int tx,
+                              int ty, int ntx, int ntiles, PhaseSpaceSpec ps,
+                              double *hist, cudaStream_t stream);
+
 template <typename R>
 cudaError_t launch_compact(SpeciesDev<R> sp_host_copy, int buf, int tx,
                            int ty, int ntx, int tile0, int ntiles,

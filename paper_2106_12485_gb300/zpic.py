@@ -20,6 +20,7 @@ OK, EINVAL, ECFL, ENOMEM, ECUDA, EOVERFLOW, ENAN, ETIMEOUT, ECAP, ENOTSUP = (
 FP32, FP64 = 0, 1
 BC_PERIODIC, BC_OPEN = 0, 1
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ = range(9)
+EB_NAMES = ("ex", "ey", "ez", "bx", "by", "bz")
 FIELD_IDS = {"ex": EX, "ey": EY, "ez": EZ, "bx": BX, "by": BY, "bz": BZ,
              "jx": JX, "jy": JY, "jz": JZ}
 PROFILE_NONE, PROFILE_UNIFORM, PROFILE_SLAB, PROFILE_RAMP = 0, 1, 2, 3
@@ -80,6 +81,15 @@ class zpic_info(C.Structure):
                 ("resorts", C.c_int32), ("device_bytes", C.c_size_t)]
 
 
+class zpic_state(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_shift", C.c_int32),
+                ("reserved", C.c_int32),
+                ("removed", C.c_int64 * MAX_SPECIES)]
+
+
+PS_X, PS_Y, PS_UX, PS_UY, PS_UZ = range(5)
+PS_IDS = {"x": PS_X, "y": PS_Y, "ux": PS_UX, "uy": PS_UY, "uz": PS_UZ}
+
 _P = C.c_void_p
 _PROTOS = {
     "zpic_create": (C.c_int, [C.POINTER(zpic_config), C.POINTER(_P)]),
@@ -104,6 +114,10 @@ _PROTOS = {
     "zpic_field_energy_noalloc_f32": (C.c_int, [_P] * 6 + [
         C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P]),
     "zpic_get_tile_counts": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
+    "zpic_get_state": (C.c_int, [_P, C.POINTER(zpic_state)]),
+    "zpic_set_state": (C.c_int, [_P, C.POINTER(zpic_state)]),
+    "zpic_phasespace": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int,
+                                  C.c_int, _P, C.c_size_t]),
     "zpic_profile_enable": (C.c_int, [_P, C.c_int]),
     "zpic_profile_read": (C.c_int, [_P, _P, C.c_size_t, _P, _P, C.c_int,
                                     C.POINTER(C.c_int), C.c_int]),
@@ -218,6 +232,7 @@ class Sim:
             check(lib().zpic_create(C.byref(cfg), C.byref(h)), "zpic_create")
             self.h = h
             self.owned = True
+        self._tracks_ids = cfg is None or bool(cfg.flags & TRACK_IDS)
         self._info_cache = None
 
     def close(self):
@@ -342,6 +357,47 @@ class Sim:
               "zpic_get_tile_counts")
         return out
 
+    # checkpoint / restart
+    def state(self):
+        st = zpic_state()
+        check(lib().zpic_get_state(self.h, C.byref(st)), "zpic_get_state")
+        return st
+
+    def set_state(self, st):
+        check(lib().zpic_set_state(self.h, C.byref(st)), "zpic_set_state")
+
+    def save_checkpoint(self, path):
+        """Writes fields E, B, every species' particles and the run state to
+        `path` (numpy .npz); restore with load_checkpoint(cfg, path)."""
+        i = self.info()
+        arrays = {"f_" + k: self.field(k) for k in EB_NAMES}
+        for s in range(i.n_species):
+            for k, v in self.particles(s).items():
+                # weights only when some differ from 1, ids only when tracked
+                if k == "w" and np.all(v == 1):
+                    continue
+                if k == "id" and not self._tracks_ids:
+                    continue
+                arrays["p%d_%s" % (s, k)] = v
+        st = self.state()
+        arrays["state"] = np.array([st.step, st.n_shift] + list(st.removed),
+                                   dtype=np.int64)
+        arrays["n_species"] = np.array([i.n_species])
+        np.savez(path, **arrays)
+
+    # diagnostics
+    def phasespace(self, s, qx, qy, range_, bins):
+        """Charge density |q0| w per bin of quantities qx, qy ("x", "y", "ux",
+        "uy", "uz"; positions in cells) over range_ = (xlo, xhi, ylo, yhi),
+        bins = (nbx, nby): an (nby, nbx) array computed on the device."""
+        nbx, nby = bins
+        out = np.zeros((nby, nbx))
+        rg = np.ascontiguousarray(range_, dtype=np.float64)
+        check(lib().zpic_phasespace(self.h, s, PS_IDS[qx], PS_IDS[qy],
+                                    _ptr(rg), nbx, nby, _ptr(out), out.size),
+              "zpic_phasespace")
+        return out
+
     def profile_enable(self, on=True):
         check(lib().zpic_profile_enable(self.h, 1 if on else 0),
               "zpic_profile_enable")
@@ -360,6 +416,26 @@ class Sim:
             nm = names.raw[k * nl:(k + 1) * nl].split(b"\0")[0].decode()
             out[nm] = (float(ms[k]), int(la[k]))
         return out
+
+
+def load_checkpoint(cfg, path):
+    """A Sim created from cfg and restored from save_checkpoint's file."""
+    d = np.load(path)
+    sim = Sim(cfg)
+    st = zpic_state()
+    v = d["state"]
+    st.step, st.n_shift = int(v[0]), int(v[1])
+    for s in range(MAX_SPECIES):
+        st.removed[s] = int(v[2 + s])
+    sim.set_state(st)
+    for k in EB_NAMES:
+        sim.set_field(k, d["f_" + k])
+    for s in range(int(d["n_species"][0])):
+        p = {k: d["p%d_%s" % (s, k)]
+             for k in ("ix", "iy", "x", "y", "ux", "uy", "uz", "w", "id")
+             if "p%d_%s" % (s, k) in d}
+        sim.set_particles(s, p)
+    return sim
 
 
 class Batch:

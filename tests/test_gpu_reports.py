@@ -1,0 +1,135 @@
+"""GPU checks (through the C ABI) of the phase-space report against the
+oracle's definition, and of checkpoint / restart: a run interrupted, saved,
+restored into a new handle and continued matches the uninterrupted run."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_12485_gb300 import workloads as W
+from paper_2106_12485_gb300 import zpic as Z
+from tests import pichelpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_state(sim, s):
+    p = sim.particles(s, dtype=np.float64)
+    return p
+
+
+@pytest.mark.parametrize("precision", [Z.FP32, Z.FP64])
+def test_phasespace_matches_oracle(precision):
+    cfg = W.clouds(96, 64, ppc=(3, 3), precision=precision, track_ids=True)
+    sim = Z.Sim(cfg)
+    sim.step(7)
+    q0 = -1.0 / 9
+    for s in range(cfg.n_species):
+        st = gpu_state(sim, s)
+        for qx, qy, rg, bins in (("x", "ux", (0, 96, -0.6, 0.6), (48, 40)),
+                                 ("x", "y", (0, 96, 0, 64), (96, 64)),
+                                 ("uy", "uz", (-0.2, 0.25, -0.3, 0.3), (17, 9))):
+            got = sim.phasespace(s, qx, qy, rg, bins)
+            want = O.phasespace(st, q0, qx, qy, rg, bins)
+            # every particle adds exactly 1/9: sums of equal terms agree to
+            # rounding whatever the order (bins decide identically, in FP64)
+            np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+            assert np.count_nonzero(got) == np.count_nonzero(want)
+    # charge inside a range that covers everything = particles x |q0|
+    n = sim.num_particles(0)
+    tot = sim.phasespace(0, "x", "y", (0, 96, 0, 64), (1, 1))
+    assert tot[0, 0] == pytest.approx(n / 9.0, rel=1e-11)  # n adds of 1/9
+
+
+def test_phasespace_weighted_window_plasma():
+    # the LWFA ramp gives weights < 1 to the injected particles
+    cfg = W.lwfa(nx=256, ny=16, track_ids=True)
+    sim = Z.Sim(cfg)
+    sim.step(300)
+    st = gpu_state(sim, 0)
+    assert np.any(st["w"] < 1)
+    q0 = -1.0 / 4
+    for qx, qy, rg, bins in (("x", "ux", (0, 256, -0.5, 0.5), (64, 32)),
+                             ("x", "uy", (100, 256, -1, 1), (39, 7))):
+        got = sim.phasespace(0, qx, qy, rg, bins)
+        want = O.phasespace(st, q0, qx, qy, rg, bins)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+def test_phasespace_argument_errors():
+    sim = Z.Sim(W.uniform_thermal(32, 32))
+    import ctypes as C
+    out = np.zeros(16)
+    rg = np.array([0.0, 1.0, 0.0, 1.0])
+    L = Z.lib()
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert L.zpic_phasespace(sim.h, 0, 9, 0, ptr(rg), 4, 4, ptr(out), 16) == Z.EINVAL
+    assert L.zpic_phasespace(sim.h, 3, 0, 1, ptr(rg), 4, 4, ptr(out), 16) == Z.EINVAL
+    assert L.zpic_phasespace(sim.h, 0, 0, 1, ptr(rg), 0, 4, ptr(out), 16) == Z.EINVAL
+    assert L.zpic_phasespace(sim.h, 0, 0, 1, ptr(rg), 4, 4, ptr(out), 15) == Z.ECAP
+    bad = np.array([1.0, 1.0, 0.0, 1.0])
+    assert L.zpic_phasespace(sim.h, 0, 0, 1, ptr(bad), 4, 4, ptr(out), 16) == Z.EINVAL
+
+
+def restart_pair(cfg, n_before, n_after, tmp_path):
+    ref = Z.Sim(cfg)
+    ref.step(n_before + n_after)
+    run = Z.Sim(cfg)
+    run.step(n_before)
+    path = str(tmp_path / "ckpt.npz")
+    run.save_checkpoint(path)
+    st = run.state()
+    del run
+    back = Z.load_checkpoint(cfg, path)
+    st2 = back.state()
+    assert (st2.step, st2.n_shift) == (st.step, st.n_shift)
+    assert list(st2.removed) == list(st.removed)
+    back.step(n_after)
+    return ref, back
+
+
+@pytest.mark.parametrize("n_before", [12, 13])   # even and odd step parity
+def test_restart_continues_the_run(n_before, tmp_path):
+    cfg = W.uniform_thermal(64, 48, ppc=(3, 3), track_ids=True, energy_every=4)
+    ref, back = restart_pair(cfg, n_before, 9, tmp_path)
+    assert back.info().step == ref.info().step == n_before + 9
+    # same arithmetic on the same inputs; only the order of the float
+    # additions into global J (tiles meeting at guard cells) may differ
+    for k in H.FIELDS:
+        assert H.rel_l2(back.field(k), ref.field(k)) < 1e-5, k
+    a, b = H.by_id(back.particles(0)), H.by_id(ref.particles(0))
+    np.testing.assert_array_equal(a["id"], b["id"])
+    for k in ("ux", "uy", "uz"):
+        np.testing.assert_allclose(a[k], b[k], rtol=0, atol=1e-5)
+    pa = a["ix"] + a["x"].astype(np.float64)
+    pb = b["ix"] + b["x"].astype(np.float64)
+    d = np.abs(pa - pb)
+    d = np.minimum(d, 64 - d)
+    assert d.max() < 1e-5
+    # the energy history restarts with the restored run
+    recs = back.energy()
+    assert recs and recs[0][0] > n_before
+
+
+def test_restart_moving_window_fp64(tmp_path):
+    # window shifts, injection and removal counts carry over exactly
+    cfg = W.lwfa(nx=256, ny=16, precision=Z.FP64, track_ids=True)
+    ref, back = restart_pair(cfg, 151, 60, tmp_path)
+    assert back.info().n_shift == ref.info().n_shift > 190
+    assert back.num_particles(0) == ref.num_particles(0)
+    assert list(back.state().removed) == list(ref.state().removed)
+    for k in H.FIELDS:
+        assert H.rel_l2(back.field(k), ref.field(k)) < 1e-12, k
+
+
+def test_set_state_errors():
+    import ctypes as C
+    sim = Z.Sim(W.uniform_thermal(32, 32))
+    st = Z.zpic_state()
+    st.step = -1
+    assert Z.lib().zpic_set_state(sim.h, C.byref(st)) == Z.EINVAL
+    st.step, st.n_shift = 4, -2
+    assert Z.lib().zpic_set_state(sim.h, C.byref(st)) == Z.EINVAL
+    batch = Z.Batch([W.uniform_thermal(32, 32), W.uniform_thermal(32, 32)])
+    st.n_shift = 0
+    assert Z.lib().zpic_set_state(batch.sim(0).h, C.byref(st)) == Z.EINVAL
+    assert Z.lib().zpic_get_state(sim.h, None) == Z.EINVAL
