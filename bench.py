@@ -99,6 +99,14 @@ def all_sum(v, world):
     return float(t.item())
 
 
+def aggregate(local_units, local_ms, world):
+    """Whole-job rate of N ranks: the units all ranks processed over the
+    slowest rank's time.  Returns (value per second, max ms, total units)."""
+    ms_max = all_max(local_ms, world)
+    total = all_sum(float(local_units), world)
+    return total / (ms_max / 1e3), ms_max, total
+
+
 # ------------------------------------------------------------- clocks ----
 
 class ClockSampler:
@@ -476,9 +484,7 @@ def main():
     resorts_timed = sim.info().resorts - resorts0
     prof = sim.profile_read(reset=True)
     sim.profile_enable(False)
-    ms_max = all_max(ms, world)
-    total_ps = all_sum(float(n_p) * args.steps, world)
-    value = total_ps / (ms_max / 1e3)
+    value, ms_max, total_ps = aggregate(float(n_p) * args.steps, ms, world)
     launches = sum(v[1] for v in prof.values())
 
     push_ms, push_n = prof.get("push_deposit", (0.0, 0))
