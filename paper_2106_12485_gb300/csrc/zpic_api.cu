@@ -871,13 +871,8 @@ class Batch : public BatchBase {
         cnt[t] = cb > ca ? (cb - ca) * th * ppc : 0;
       }
       const double nominal = (double)ppc * S.tx * S.ty;
-      // room to grow; a species the moving window injects will fill every
-      // tile to its full density, so its tiles start with that room
-      const bool injected = c.moving_window && P.cfg.profile != ZPIC_PROFILE_NONE;
-      const int min_extra = std::max(
-          64, (int)std::ceil(nominal * (injected ? 1.0 + slack : slack)));
       P.ob_cap = ((std::max(64, (int)std::ceil(nominal * (c.moving_window ? 0.25 : 0.125))) + 31) / 32) * 32;
-      ZP_TRY(alloc_store(i, s, cnt, slack, min_extra));
+      ZP_TRY(alloc_store(i, s, cnt, slack, full_tile_cap(nominal, slack)));
       // the initial load writes cnt particles per tile directly
       ZP_CU(cudaMemcpyAsync(P.cnt.p, cnt.data(), sizeof(int) * S.ntiles,
                             cudaMemcpyHostToDevice, stream_));
@@ -938,15 +933,25 @@ class Batch : public BatchBase {
   }
 
   // Allocates the tile store of species s for per-tile counts cnt.
+  static int full_tile_cap(double nominal, double slack) {
+    return std::max(64, (int)std::ceil(nominal * (1.0 + slack)));
+  }
+
+  // Capacity of tile t: room for its count plus the slack, and at least
+  // min_cap, the species' full density of a tile plus the slack.  An empty
+  // tile can thus fill at the species' density (a cloud front moving in, a
+  // window injecting plasma) without a re-sort; only compression beyond
+  // that density overflows.
   int alloc_store(int si, int s, const std::vector<int> &cnt, double slack,
-                  int min_extra) {
+                  int min_cap) {
     SimHost<R> &S = sims_[si];
     SpeciesHost<R> &P = S.sp[s];
     std::vector<int> off(S.ntiles), cap(S.ntiles);
     long long tot = 0;
     for (int t = 0; t < S.ntiles; ++t) {
       long long c = std::max<long long>((long long)std::ceil(cnt[t] * (1.0 + slack)),
-                                        (long long)cnt[t] + min_extra);
+                                        (long long)cnt[t] + 64);
+      c = std::max<long long>(c, min_cap);
       // a tile that outgrew its capacity at least doubles it, so a tile that
       // keeps filling (a moving front) needs few re-sorts
       if (!P.h_cap.empty() && cnt[t] > P.h_cap[t])
@@ -1217,11 +1222,7 @@ class Batch : public BatchBase {
       return fail(ZPIC_EINVAL, "particles outside the grid or offsets not in [0,1)");
     const double slack = S.cfg.capacity_slack > 0 ? S.cfg.capacity_slack : 0.25;
     const double nominal = (double)P.cfg.ppc_x * P.cfg.ppc_y * S.tx * S.ty;
-    const bool injected =
-        S.cfg.moving_window && P.cfg.profile != ZPIC_PROFILE_NONE;
-    ZP_TRY(alloc_store(si, s, cnt, slack,
-                       std::max(64, (int)std::ceil(
-                                        nominal * (injected ? 1.0 + slack : slack)))));
+    ZP_TRY(alloc_store(si, s, cnt, slack, full_tile_cap(nominal, slack)));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1, S.tx,

@@ -128,9 +128,11 @@ def test_migration_invariants():
 
 
 def test_overflow_recovery_matches_oracle():
-    # a drifting beam into an empty region overflows tiny tile capacities
+    # a beam at four times the configured density (8x8 particles per cell
+    # against 4x4) drifts into empty tiles, whose capacity is the configured
+    # full density plus 1 %: they overflow and the host re-sorts
     nx, ny = 64, 32
-    ld = P.plasma_load(nx, ny, 4, 4, u_th=(0.05, 0.05, 0.05),
+    ld = P.plasma_load(nx, ny, 8, 8, u_th=(0.05, 0.05, 0.05),
                        u_fl=(0.9, 0.0, 0.0), x_range=(0, 8))
     cfg = cfg_for_loads(nx, ny, (0.1, 0.1), 0.07, [(-1.0, (4, 4))],
                         tile=(8, 8), capacity_slack=0.01)
