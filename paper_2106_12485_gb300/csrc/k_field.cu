@@ -36,6 +36,19 @@ __device__ __forceinline__ R fld(const SimDev<R> &S, const R *f, int gi,
   return f[(size_t)gj * S.ld + gi];
 }
 
+// the same boundary rules for this step's deposited current
+template <typename R>
+__device__ __forceinline__ R fld_j(const SimDev<R> &S, int cur, int c, int gi,
+                                   int gj) {
+  gj = wrapg(gj, S.ny);
+  if (S.open_x) {
+    if (gi < 0 || gi >= S.nx) return R(0);
+  } else {
+    gi = wrapg(gi, S.nx);
+  }
+  return j_value(S, cur, c, (size_t)gj * S.ld + gi);
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -84,11 +97,12 @@ __global__ void __launch_bounds__(kThreads)
     sb[c][lj][li] = fld(S, S.B[cur][c], x0 - 1 + li, y0 - 1 + lj);
   }
   // the current that drives E: this step's deposit, or its filtered copy
-  const R *const *jsrc = S.Jf[0] ? S.Jf : S.J[cur];
+  const bool filtered = S.Jf[0] != nullptr;
   for (int k = threadIdx.x; k < 3 * JH * JW; k += blockDim.x) {
     const int c = k / (JH * JW), r = k - c * (JH * JW);
     const int lj = r / JW, li = r - lj * JW;
-    sj[c][lj][li] = fld(S, jsrc[c], x0 + li, y0 + lj);
+    sj[c][lj][li] = filtered ? fld(S, S.Jf[c], x0 + li, y0 + lj)
+                             : fld_j(S, cur, c, x0 + li, y0 + lj);
   }
   __syncthreads();
 
@@ -161,7 +175,12 @@ __global__ void __launch_bounds__(kThreads)
         S.B[nxt][c][row + gi] = R(0);
       }
     }
-    for (int c = 0; c < 3; ++c) S.J[nxt][c][row + gi] = R(0);
+    for (int c = 0; c < 3; ++c) {
+      if constexpr (sizeof(R) == 4)
+        S.Jq[nxt][c][row + gi] = 0;
+      else
+        S.J[nxt][c][row + gi] = R(0);
+    }
   }
   if (do_energy) {
     const size_t b = (size_t)it.y * 2;
@@ -200,7 +219,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int c = 0; c < 3; ++c) {
     for (int k = threadIdx.x; k < H * W; k += blockDim.x) {
       const int lj = k / W, li = k - lj * W;
-      a[lj][li] = fld(S, S.J[cur][c], x0 - 2 + li, y0 - 2 + lj);
+      a[lj][li] = fld_j(S, cur, c, x0 - 2 + li, y0 - 2 + lj);
     }
     __syncthreads();
     // x binomial on local columns 1..W-2 (global x0 - 1 .. x0 + X)

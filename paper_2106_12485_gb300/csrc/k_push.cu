@@ -23,6 +23,8 @@
 //     with one reduction per cell (periodic images folded here).
 // Traffic per particle: one read and one write of its SoA record (16-bit
 // cell within the tile + 5 reals: 22 bytes in FP32).
+#include <type_traits>
+
 #include "zpic_dev.cuh"
 #include "zpic_kernels.h"
 
@@ -98,16 +100,25 @@ struct TileJ<float> {
   }
   // value of word idx (plane c, position r in the plane), 2^-30 units;
   // returns false when it is zero
+  // value of word (plane c, position r in the plane) in 2^-30 units;
+  // returns false when it is zero
   __device__ __forceinline__ bool value(int c, int r, int JW, int JP,
-                                        double &v) const {
+                                        long long &v) const {
     unsigned n = (unsigned)cnt[r];
     if (r >= 1 && c != 0) n += (unsigned)cnt[r - 1];
     if (r >= JW && c != 1) n += (unsigned)cnt[r - JW];
     if (r >= JW + 1 && c == 2) n += (unsigned)cnt[r - JW - 1];
     const int h = (int)((unsigned)hi[c * JP + r] - n * kBias);
     const int l = (int)((unsigned)lo[c * JP + r] - n * kBias);
-    v = (double)h * 16384.0 + (double)l;
+    v = (long long)h * 16384 + l;
     return (h | l) != 0;
+  }
+  // adds the value of a word to the global fixed-point sum (exact: the sum
+  // does not depend on the order in which tiles add)
+  __device__ __forceinline__ static void fold(const SimDev<float> &S, int cur,
+                                              int c, size_t o, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(S.Jq[cur][c] + o),
+              (unsigned long long)v);
   }
   __device__ __forceinline__ void zero(int JP) const {
     for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) {
@@ -129,6 +140,11 @@ struct TileJ<double> {
                                         double &out) const {
     out = v[c * JP + r];
     return out != 0.0;
+  }
+  __device__ __forceinline__ static void fold(const SimDev<double> &S,
+                                              int cur, int c, size_t o,
+                                              double v) {
+    atomicAdd(S.J[cur][c] + o, v);
   }
   __device__ __forceinline__ void zero(int JP) const {
     for (int k = threadIdx.x; k < 3 * JP; k += blockDim.x) v[k] = 0.0;
@@ -815,9 +831,8 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
     const size_t o = (size_t)gj * ld + gi;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double v;
-      if (T.jt.value(c, r, JW, JP, v))
-        atomicAdd(S.J[CUR][c] + o, (R)(v * S.jscale[c]));
+      typename std::conditional<sizeof(R) == 4, long long, double>::type v;
+      if (T.jt.value(c, r, JW, JP, v)) TileJ<R>::fold(S, CUR, c, o, v);
     }
   }
 }

@@ -372,9 +372,13 @@ class Batch : public BatchBase {
     const R *src;
     if (which < 6)
       src = which < 3 ? S.dev.E[step & 1][which] : S.dev.B[step & 1][which - 3];
+    else if (S.dev.Jf[0])
+      src = S.dev.Jf[which - 6];  // the filtered current
+    else if (sizeof(R) == 4)
+      return get_current_fixed(S, S.dev.Jq[(step + 1) & 1][which - 6],
+                               S.dev.jscale[which - 6], dst, want_f64);
     else
-      src = S.dev.Jf[0] ? S.dev.Jf[which - 6]     // the filtered current
-                        : S.dev.J[(step + 1) & 1][which - 6];  // last step's
+      src = S.dev.J[(step + 1) & 1][which - 6];  // last step's current
     const bool same = want_f64 == (sizeof(R) == 8);
     if (same) {
       ZP_CU(cudaMemcpy2DAsync(dst, S.nx * sizeof(R), src, S.ld * sizeof(R),
@@ -394,6 +398,26 @@ class Batch : public BatchBase {
     } else {
       float *d = (float *)dst;
       for (size_t k = 0; k < n; ++k) d[k] = (float)tmp[k];
+    }
+    return ZPIC_OK;
+  }
+
+  // FP32 current: int64 fixed-point sums, scaled as the kernels do (a
+  // double product rounded to float)
+  int get_current_fixed(SimHost<R> &S, const long long *src, double scale,
+                        void *dst, int want_f64) {
+    const size_t n = (size_t)S.nx * S.ny;
+    std::vector<long long> q(n);
+    ZP_CU(cudaMemcpy2DAsync(q.data(), S.nx * sizeof(long long), src,
+                            S.ld * sizeof(long long), S.nx * sizeof(long long),
+                            S.ny, cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    for (size_t k = 0; k < n; ++k) {
+      const float v = (float)((double)q[k] * scale);
+      if (want_f64)
+        ((double *)dst)[k] = v;
+      else
+        ((float *)dst)[k] = v;
     }
     return ZPIC_OK;
   }
@@ -648,6 +672,7 @@ class Batch : public BatchBase {
         std::swap(S.dev.E[0][c], S.dev.E[1][c]);
         std::swap(S.dev.B[0][c], S.dev.B[1][c]);
         std::swap(S.dev.J[0][c], S.dev.J[1][c]);
+        std::swap(S.dev.Jq[0][c], S.dev.Jq[1][c]);
       }
       for (int s = 0; s < (int)S.sp.size(); ++s) {
         std::swap(S.dev.sp[s].buf[0], S.dev.sp[s].buf[1]);
@@ -793,7 +818,10 @@ class Batch : public BatchBase {
     S.yby = (S.ny + kYeeY - 1) / kYeeY;
     const size_t plane = (size_t)S.ny * S.ld;
     const bool filter = (c.flags & ZPIC_FILTER_J) != 0;
-    if (!dalloc(S.fields, (filter ? 21 : 18) * plane * sizeof(R)))
+    // E, B: 12 planes of R; J: 6 planes of 8-byte values; Jf: 3 planes of R
+    const size_t eb_bytes = 12 * plane * sizeof(R);
+    const size_t j_bytes = 6 * plane * 8;
+    if (!dalloc(S.fields, eb_bytes + j_bytes + (filter ? 3 * plane * sizeof(R) : 0)))
       return fail(ZPIC_ENOMEM, "fields");
     ZP_CU(cudaMemsetAsync(S.fields.p, 0, S.fields.bytes, stream_));
     R *f = (R *)S.fields.p;
@@ -819,14 +847,18 @@ class Batch : public BatchBase {
     D.dx_d = S.dx;
     D.dy_d = S.dy;
     D.dt_d = S.dt;
+    char *jb = (char *)S.fields.p + eb_bytes;
     for (int a = 0; a < 2; ++a)
       for (int c3 = 0; c3 < 3; ++c3) {
-        D.E[a][c3] = f + (size_t)(a * 9 + c3) * plane;
-        D.B[a][c3] = f + (size_t)(a * 9 + 3 + c3) * plane;
-        D.J[a][c3] = f + (size_t)(a * 9 + 6 + c3) * plane;
+        D.E[a][c3] = f + (size_t)(a * 6 + c3) * plane;
+        D.B[a][c3] = f + (size_t)(a * 6 + 3 + c3) * plane;
+        char *j = jb + (size_t)(a * 3 + c3) * plane * 8;
+        D.Jq[a][c3] = sizeof(R) == 4 ? (long long *)j : nullptr;
+        D.J[a][c3] = sizeof(R) == 8 ? (R *)j : nullptr;
       }
+    R *jf = (R *)(jb + j_bytes);
     for (int c3 = 0; c3 < 3; ++c3)
-      D.Jf[c3] = filter ? f + (size_t)(18 + c3) * plane : nullptr;
+      D.Jf[c3] = filter ? jf + (size_t)c3 * plane : nullptr;
     if (!dalloc(S.part_kin, sizeof(double) * S.ntiles * kMaxSpecies) ||
         !dalloc(S.part_fld, sizeof(double) * 2 * S.ybx * S.yby))
       return fail(ZPIC_ENOMEM, "partials");

@@ -8,8 +8,9 @@
 // HBM layout per simulation (R = float or double):
 //   fields: E[2][3], B[2][3], J[2][3] arrays of ny rows x ld (ld = nx padded
 //           to 128 bytes); copy (step & 1) is current, the Yee kernel
-//           writes copy (step & 1) ^ 1 (ping-pong, no halo races); with the
-//           current filter on, 3 more arrays Jf hold the filtered J;
+//           writes copy (step & 1) ^ 1 (ping-pong, no halo races); J holds
+//           8-byte values (int64 fixed point in FP32, double in FP64); with
+//           the current filter on, 3 more arrays Jf hold the filtered J;
 //   particles, per species: SoA arrays cell (uint16, cell within the tile),
 //           x, y, ux, uy, uz (R), optional w (R) and id (int32), one segment per
 //           tile [off[t], off[t] + cap[t]) of which cnt[t] are live; two
@@ -94,11 +95,17 @@ struct SimDev {
   R dx, dy, dt;
   R dt_dx, dt_dy;              // dt/dx, dt/dy (cells per unit velocity)
   double dx_d, dy_d, dt_d;     // double values (window schedule, setup)
-  R *E[2][3], *B[2][3], *J[2][3];
+  R *E[2][3], *B[2][3];
+  // deposited current, two copies: FP32 keeps exact fixed-point sums in
+  // int64 (units of 2^-30, scaled by jscale when read), so its value does
+  // not depend on the order of the tiles' adds; FP64 keeps doubles
+  long long *Jq[2][3];         // FP32 (null in FP64)
+  R *J[2][3];                  // FP64 (null in FP32)
   R *Jf[3];                    // filtered current (null: no filter)
   // FP32 tiles accumulate J exactly in two-word fixed point with 2^-30 units
   // of Uq dx/dt, Uq dy/dt, Uq (Uq = max |q0| x max weight, so one segment
-  // contributes at most one unit); jscale converts a tile sum to J.
+  // contributes at most one unit) and add it to Jq; jscale converts a sum
+  // to J.
   double jscale[3];
   double *part_kin;            // [ntiles][kMaxSpecies] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
@@ -135,6 +142,16 @@ __device__ __forceinline__ bool shift_due(const SimDev<R> &S, int step,
                                           int n_shift) {
   return S.moving_window &&
          ((double)(step + 1) * S.dt_d >= (double)(n_shift + 1) * S.dx_d);
+}
+
+// This step's deposited current of component c at array index idx, as R.
+template <typename R>
+__device__ __forceinline__ R j_value(const SimDev<R> &S, int cur, int c,
+                                     size_t idx) {
+  if constexpr (sizeof(R) == 4)
+    return (R)((double)S.Jq[cur][c][idx] * S.jscale[c]);
+  else
+    return S.J[cur][c][idx];
 }
 
 __device__ __forceinline__ bool frozen(const BatchStatus *st, int step) {
