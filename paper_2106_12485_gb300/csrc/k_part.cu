@@ -14,9 +14,14 @@ namespace zp {
 //
 // One CTA per tile: scans the outboxes of its distinct neighbour tiles, keeps
 // the entries whose cell lies in this tile and appends them behind the tile's
-// stayers (warp-aggregated slot claims on a shared cursor).  Tiles in the last
-// column also receive the new plasma column when the window shifts.  Particles
-// that find no room go to the overflow buffer and raise ERR_OVERFLOW.
+// stayers.  The neighbours' outboxes are read as one concatenated list in
+// passes of kMigE entries per thread: all entries of a pass are loaded
+// first, a block-wide prefix sum of the kept entries gives their slots, then
+// they are copied, so a tile waits for a few memory round trips instead of
+// one per neighbour, and the order of the arrivals is fixed.  Tiles in the
+// last column also receive the new plasma column when the window shifts.
+// Particles that find no room go to the overflow buffer and raise
+// ERR_OVERFLOW.
 
 template <typename R>
 __device__ __forceinline__ void park(OverflowDev<R> &ovf, BatchStatus *st,
@@ -52,6 +57,35 @@ __device__ __forceinline__ double window_density(const SpeciesDev<R> &P,
   return P.n0;
 }
 
+constexpr int kMigE = 8;  // outbox entries per thread and pass
+constexpr int kPT_MIG = kThreads;
+
+// Exclusive prefix sum of v over the CTA (kThreads threads); total = sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *wsum,
+                                                    int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kWarps ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kWarps) wsum[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  const int before = warp > 0 ? wsum[warp - 1] : 0;
+  total = wsum[kWarps - 1];
+  __syncthreads();  // wsum is reused by the next call
+  return before + x - v;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     migrate_kernel(const SimDev<R> *__restrict__ sims,
@@ -59,6 +93,8 @@ __global__ void __launch_bounds__(kThreads)
                    OverflowDev<R> ovf) {
   __shared__ int nbl[8];
   __shared__ int nnb;
+  __shared__ int pre[9];  // prefix of the neighbours' outbox counts
+  __shared__ int wsum[kWarps];
   __shared__ int cursor;
   const int step = st->step;
   if (frozen(st, step)) return;
@@ -98,35 +134,44 @@ __global__ void __launch_bounds__(kThreads)
     const SpeciesDev<R> &P = S.sp[s];
     const Planes<R> &O = P.buf[nxt];
     __syncthreads();
-    if (threadIdx.x == 0) cursor = 0;
+    if (threadIdx.x == 0) {
+      pre[0] = 0;
+      for (int q = 0; q < nnb; ++q) pre[q + 1] = pre[q] + P.ob_cnt[nbl[q]];
+    }
     __syncthreads();
     const int n_stay = P.cnt[tile];
     const int cap = P.cap[tile];
     const size_t base = (size_t)P.off[tile];
-    for (int q = 0; q < nnb; ++q) {
-      const int nb = nbl[q];
-      const int m = P.ob_cnt[nb];
-      const size_t ob = (size_t)nb * P.ob_cap;
-      for (int k0 = 0; k0 < m; k0 += blockDim.x) {
-        const int k = k0 + threadIdx.x;
-        bool mine = false;
-        int ix = 0, iy = 0;
-        if (k < m) {
-          ix = P.ob_ix[ob + k];
-          iy = P.ob_iy[ob + k];
-          mine = (iy / S.ty) * S.ntx + ix / S.tx == tile;
+    const int m_all = pre[nnb];
+    int placed = 0;  // arrivals placed by earlier passes (CTA-uniform)
+    for (int k0 = 0; k0 < m_all; k0 += kPT_MIG * kMigE) {
+      // pass: load the destination cells of up to kMigE entries per thread
+      int ent[kMigE];
+      unsigned keep = 0;
+#pragma unroll
+      for (int j = 0; j < kMigE; ++j) {
+        const int k = k0 + j * kPT_MIG + threadIdx.x;
+        ent[j] = -1;
+        if (k < m_all) {
+          int q = 0;
+          while (q + 1 < nnb && pre[q + 1] <= k) ++q;
+          const int e = nbl[q] * P.ob_cap + (k - pre[q]);
+          ent[j] = e;
+          const int ix = P.ob_ix[e], iy = P.ob_iy[e];
+          if ((iy / S.ty) * S.ntx + ix / S.tx == tile) keep |= 1u << j;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, mine);
-        if (!bal) continue;
-        const int leader = __ffs(bal) - 1;
-        int wb = 0;
-        if (lane == leader) wb = atomicAdd(&cursor, __popc(bal));
-        wb = __shfl_sync(0xffffffffu, wb, leader);
-        if (!mine) continue;
-        const size_t e = ob + k;
-        const int d = n_stay + wb + __popc(bal & lt);
+      }
+      int total;
+      const int first = block_exclusive_scan(__popc(keep), wsum, total);
+      int r = 0;
+#pragma unroll
+      for (int j = 0; j < kMigE; ++j) {
+        if (!(keep & (1u << j))) continue;
+        const int e = ent[j];
+        const int ix = P.ob_ix[e], iy = P.ob_iy[e];
         const R w = O.w ? P.ob_w[e] : R(1);
         const int id = O.id ? P.ob_id[e] : 0;
+        const int d = n_stay + placed + first + r++;
         if (d < cap) {
           const size_t t = base + d;
           O.cell[t] = local_cell(ix - x0, iy - y0);
@@ -142,7 +187,10 @@ __global__ void __launch_bounds__(kThreads)
                P.ob_ux[e], P.ob_uy[e], P.ob_uz[e], w);
         }
       }
+      placed += total;
     }
+    if (threadIdx.x == 0) cursor = placed;
+    __syncthreads();
     // moving window: cold plasma on a lattice enters through column nx-1
     if (inject_col && P.inj_ppc_x > 0) {
       const int ppx = P.inj_ppc_x, ppc = ppx * P.inj_ppc_y;

@@ -904,6 +904,8 @@ class Batch : public BatchBase {
       }
       const double nominal = (double)ppc * S.tx * S.ty;
       P.ob_cap = ((std::max(64, (int)std::ceil(nominal * (c.moving_window ? 0.25 : 0.125))) + 31) / 32) * 32;
+      if ((long long)P.ob_cap * S.ntiles >= INT_MAX)
+        return fail(ZPIC_EINVAL, "outbox index range exceeded (grid x ppc too large)");
       ZP_TRY(alloc_store(i, s, cnt, slack, full_tile_cap(nominal, slack)));
       // the initial load writes cnt particles per tile directly
       ZP_CU(cudaMemcpyAsync(P.cnt.p, cnt.data(), sizeof(int) * S.ntiles,
