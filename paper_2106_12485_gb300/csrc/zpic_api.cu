@@ -996,16 +996,21 @@ class Batch : public BatchBase {
       cap[t] = (int)c;
       tot += c;
     }
-    // free the previous store; each copy is one block of planes
-    dfree(P.store[0]);
-    dfree(P.store[1]);
     P.total_cap = tot;
     const size_t cb = ((size_t)2 * tot + 255) & ~size_t(255);
     const size_t ib = ((size_t)4 * tot + 255) & ~size_t(255);
     const size_t rb = (sizeof(R) * (size_t)tot + 255) & ~size_t(255);
     const size_t block = cb + (P.has_id ? ib : 0) + rb * (5 + (P.has_w ? 1 : 0));
-    for (int b = 0; b < 2; ++b)
+    // each copy is one block of planes; a block that is large enough (and
+    // not more than twice too large) is kept, so a re-sort or an upload of
+    // the same size allocates nothing (the data it held is no longer needed:
+    // callers have moved the particles to the staging area)
+    for (int b = 0; b < 2; ++b) {
+      if (P.store[b].p && P.store[b].bytes >= block && P.store[b].bytes <= 2 * block)
+        continue;
+      dfree(P.store[b]);
       if (!dalloc(P.store[b], block)) return fail(ZPIC_ENOMEM, "particle store");
+    }
     if (!P.off.p) {
       if (!dalloc(P.off, 4 * S.ntiles) || !dalloc(P.cap, 4 * S.ntiles) ||
           !dalloc(P.cnt, 4 * S.ntiles) || !dalloc(P.ob_cnt, 4 * S.ntiles))
@@ -1107,13 +1112,19 @@ class Batch : public BatchBase {
 
   int upload_descriptors() {
     // the single-simulation push kernel takes the descriptor by value, so a
-    // captured graph holds a copy: capture again after any change
+    // captured graph holds a copy: capture again after any change (and only
+    // then: an upload or re-sort that leaves every descriptor as it was
+    // keeps the graph)
     ZP_CU(cudaStreamSynchronize(stream_));
-    invalidate_graph();
-    if (!sims_dev_.p && !dalloc(sims_dev_, sizeof(SimDev<R>) * n_sims))
-      return fail(ZPIC_ENOMEM, "descriptors");
     std::vector<SimDev<R>> h(n_sims);
     for (int i = 0; i < n_sims; ++i) h[i] = sims_[i].dev;
+    if (sims_dev_.p && uploaded_.size() == h.size() &&
+        std::memcmp(uploaded_.data(), h.data(), sizeof(SimDev<R>) * n_sims) == 0)
+      return ZPIC_OK;
+    invalidate_graph();
+    uploaded_ = h;
+    if (!sims_dev_.p && !dalloc(sims_dev_, sizeof(SimDev<R>) * n_sims))
+      return fail(ZPIC_ENOMEM, "descriptors");
     ZP_CU(cudaMemcpyAsync(sims_dev_.p, h.data(), sizeof(SimDev<R>) * n_sims,
                           cudaMemcpyHostToDevice, stream_));
     ZP_CU(cudaStreamSynchronize(stream_));
@@ -1477,6 +1488,7 @@ class Batch : public BatchBase {
   int n_items_ = 0, n_yee_ = 0, max_tx_ = 2, max_ty_ = 2;
   bool all16_ = false;
   BatchStatus *h_st_ = nullptr;
+  std::vector<SimDev<R>> uploaded_;  // descriptors as last uploaded
   long long target_ = 0;
   int sticky_ = ZPIC_OK;
   int resorts_ = 0;
