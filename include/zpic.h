@@ -60,6 +60,18 @@ extern "C" {
 #define ZPIC_ECAP (-8)      /* destination buffer too small               */
 #define ZPIC_ENOTSUP (-9)   /* option not supported by this build         */
 
+/* Errors that end a handle's run (ZPIC_EOVERFLOW after a failed re-sort,
+ * ZPIC_ENAN, ZPIC_ETIMEOUT, a corrupted store) are sticky: every later step
+ * or sync of that handle returns the same code.
+ *
+ * Testing hook: the environment variable ZPIC_FAULT (read at every check)
+ * injects failures on the host without touching the GPU: "alloc" makes
+ * every device allocation fail (ZPIC_ENOMEM), "launch" makes every kernel
+ * or graph launch fail before anything is launched (ZPIC_ECUDA from
+ * zpic_step; the handle stays usable once the variable is cleared),
+ * "timeout" makes zpic_sync report a bounded device wait that gave up
+ * (ZPIC_ETIMEOUT, sticky). */
+
 /* precision of fields and particle state */
 #define ZPIC_FP32 0
 #define ZPIC_FP64 1

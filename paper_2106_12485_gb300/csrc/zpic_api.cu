@@ -17,6 +17,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -56,6 +57,16 @@ static int cuda_fail(cudaError_t e, const char *what) {
     int r_ = (x);                \
     if (r_ != ZPIC_OK) return r_; \
   } while (0)
+
+// Host-side fault injection for tests (environment variable ZPIC_FAULT, read
+// at every check): "alloc" makes every device allocation fail, "launch"
+// makes every kernel or graph launch report a failure without launching
+// anything, "timeout" makes zpic_sync report a bounded device wait that gave
+// up.  Nothing reaches the GPU, so the injected failures cannot fault it.
+static bool fault(const char *kind) {
+  const char *v = std::getenv("ZPIC_FAULT");
+  return v && std::strcmp(v, kind) == 0;
+}
 
 static zpic_alloc_fn g_alloc = nullptr;
 static zpic_free_fn g_free = nullptr;
@@ -306,15 +317,21 @@ class Batch : public BatchBase {
   int step(int n) override {
     if (n < 0) return fail(ZPIC_EINVAL, "negative step count");
     if (sticky_) return sticky_;
+    ZP_TRY(enqueue(n));
     target_ += n;
-    return enqueue(n);
+    return ZPIC_OK;
   }
 
   int sync() override {
+    if (sticky_) return sticky_;
     // re-sort and re-issue as long as every round advances the step count
     int stalled = 0, last_step = -1;
     for (;;) {
       ZP_CU(cudaStreamSynchronize(stream_));
+      if (fault("timeout")) {
+        sticky_ = fail(ZPIC_ETIMEOUT, "injected: a bounded device wait gave up");
+        return sticky_;
+      }
       ZP_TRY(read_status());
       const BatchStatus &st = *h_st_;
       if (st.step == last_step) {
@@ -788,6 +805,11 @@ class Batch : public BatchBase {
   // ---- setup ---------------------------------------------------------------
 
   void *dalloc(DevMem &m, size_t bytes) {
+    if (fault("alloc")) {
+      m.p = nullptr;
+      m.bytes = 0;
+      return nullptr;
+    }
     m.p = alloc_->get(bytes, &bytes_);
     m.bytes = m.p ? bytes : 0;
     return m.p;
@@ -1354,6 +1376,7 @@ class Batch : public BatchBase {
   }
 
   cudaError_t launch_stage(int k) {
+    if (fault("launch")) return cudaErrorLaunchFailure;
     switch (k) {
       case 0:
         return launch_push_deposit<R>(dsims(), n_sims == 1 ? &sims_[0].dev : nullptr,
@@ -1405,6 +1428,7 @@ class Batch : public BatchBase {
       return ZPIC_OK;
     }
     if (!graph_exec_) ZP_TRY(capture());
+    if (fault("launch")) return cuda_fail(cudaErrorLaunchFailure, "graph launch");
     for (int i = 0; i < n; ++i) ZP_CU(cudaGraphLaunch(graph_exec_, stream_));
     return ZPIC_OK;
   }
@@ -1416,7 +1440,7 @@ class Batch : public BatchBase {
     ZP_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t keep = stream_;
     stream_ = cs;
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       for (int k : stages())
@@ -1426,7 +1450,10 @@ class Batch : public BatchBase {
     }
     stream_ = keep;
     cudaStreamDestroy(cs);
-    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e, "graph capture");
+    }
     e = cudaGraphInstantiate(&graph_exec_, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
