@@ -12,6 +12,7 @@
 // parked in the overflow buffer it re-sorts the affected stores with more
 // capacity and re-issues the steps that were held back.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -67,6 +68,13 @@ static bool fault(const char *kind) {
   const char *v = std::getenv("ZPIC_FAULT");
   return v && std::strcmp(v, kind) == 0;
 }
+
+// NVTX range over an ABI call (header-only NVTX3: free unless a profiler
+// such as Nsight Systems is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static zpic_alloc_fn g_alloc = nullptr;
 static zpic_free_fn g_free = nullptr;
@@ -1314,6 +1322,7 @@ class Batch : public BatchBase {
   // After ERR_OVERFLOW: every species of every sim with parked particles is
   // compacted, joined with its overflow entries and re-binned with more room.
   int resort_all() {
+    NvtxRange r_("zpic re-sort after tile overflow");
     const int n_ovf = std::min(h_st_->ovf_count, ovf_cap_);
     std::vector<int> osim(n_ovf), osp(n_ovf);
     if (n_ovf > 0) {
@@ -1421,6 +1430,7 @@ class Batch : public BatchBase {
           ZP_CU(cudaEventCreate(&a));
           ZP_CU(cudaEventCreate(&b));
           ZP_CU(cudaEventRecord(a, stream_));
+          NvtxRange r_(stage_name(order[t]));
           ZP_CU(launch_stage(order[t]));
           ZP_CU(cudaEventRecord(b, stream_));
           timers_[t].ev.push_back({a, b});
@@ -1434,6 +1444,7 @@ class Batch : public BatchBase {
   }
 
   int capture() {
+    NvtxRange r_("zpic graph capture");
     // kernel attributes are set outside the capture
     ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_, ring_wide()));
     cudaStream_t cs;
@@ -1558,6 +1569,7 @@ int make_batch(const zpic_config *cfgs, int n, zpic_batch **out) {
 extern "C" {
 
 int zpic_create(const zpic_config *cfg, zpic_sim **out) {
+  NvtxRange r_("zpic_create");
   if (!out) return fail(ZPIC_EINVAL, "out is NULL");
   *out = nullptr;
   zpic_batch *b = nullptr;
@@ -1575,6 +1587,7 @@ int zpic_destroy(zpic_sim *sim) {
 }
 
 int zpic_step(zpic_sim *sim, int n) {
+  NvtxRange r_("zpic_step");
   ZP_SIM(sim);
   (void)I;
   if (!sim->owns) return fail(ZPIC_EINVAL, "step a batch view with zpic_batch_step");
@@ -1582,6 +1595,7 @@ int zpic_step(zpic_sim *sim, int n) {
 }
 
 int zpic_sync(zpic_sim *sim) {
+  NvtxRange r_("zpic_sync");
   ZP_SIM(sim);
   (void)I;
   return B->sync();
@@ -1615,6 +1629,7 @@ int zpic_num_particles(zpic_sim *sim, int species, int64_t *n) {
 
 int zpic_get_particles(zpic_sim *sim, int species, const zpic_particles *dst,
                        size_t *n_written) {
+  NvtxRange r_("zpic_get_particles");
   ZP_SIM(sim);
   return B->get_particles(I, species, 0, -1, dst, n_written);
 }
@@ -1628,6 +1643,7 @@ int zpic_get_particles_tiles(zpic_sim *sim, int species, int tile_begin,
 }
 
 int zpic_set_particles(zpic_sim *sim, int species, const zpic_particles *src) {
+  NvtxRange r_("zpic_set_particles");
   ZP_SIM(sim);
   return B->set_particles(I, species, src);
 }
@@ -1689,11 +1705,13 @@ int zpic_batch_create(const zpic_config *cfgs, int n, zpic_batch **out) {
 }
 
 int zpic_batch_step(zpic_batch *b, int n) {
+  NvtxRange r_("zpic_batch_step");
   if (!b) return fail(ZPIC_EINVAL, "NULL batch");
   return b->impl->step(n);
 }
 
 int zpic_batch_sync(zpic_batch *b) {
+  NvtxRange r_("zpic_batch_sync");
   if (!b) return fail(ZPIC_EINVAL, "NULL batch");
   return b->impl->sync();
 }
