@@ -700,6 +700,7 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   if (threadIdx.x == 0) {
     P.cnt[T.tile] = T.s_slots[0];
     P.ob_cnt[T.tile] = min(T.s_slots[1], P.ob_cap);
+    if (T.s_slots[1] > P.ob_cap) atomicMax(&S.ob_need[s], T.s_slots[1]);
   }
 }
 

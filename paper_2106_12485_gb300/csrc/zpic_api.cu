@@ -905,12 +905,13 @@ class Batch : public BatchBase {
     D.hist_skip = 0;
     if (!dalloc(S.energy_rows, sizeof(double) * (2 * (size_t)S.ny + 2)))
       return fail(ZPIC_ENOMEM, "energy scratch");
-    if (!dalloc(S.small, sizeof(int) * (2 + kMaxSpecies)))
+    if (!dalloc(S.small, sizeof(int) * (2 + 2 * kMaxSpecies)))
       return fail(ZPIC_ENOMEM, "counters");
     ZP_CU(cudaMemsetAsync(S.small.p, 0, S.small.bytes, stream_));
     D.hist_n = (int *)S.small.p;
     D.n_shift = (int *)S.small.p + 1;
     D.removed = (int *)S.small.p + 2;
+    D.ob_need = (int *)S.small.p + 2 + kMaxSpecies;
 
     // species: initial per-tile counts from the profile, then capacities
     S.sp.resize(c.n_species);
@@ -936,7 +937,8 @@ class Batch : public BatchBase {
       P.ob_cap = ((std::max(64, (int)std::ceil(nominal * (c.moving_window ? 0.25 : 0.125))) + 31) / 32) * 32;
       if ((long long)P.ob_cap * S.ntiles >= INT_MAX)
         return fail(ZPIC_EINVAL, "outbox index range exceeded (grid x ppc too large)");
-      ZP_TRY(alloc_store(i, s, cnt, slack, full_tile_cap(nominal, slack)));
+      ZP_TRY(alloc_store(i, s, cnt, slack, nominal,
+                         full_tile_cap(nominal, slack, window_plasma(S, P))));
       // the initial load writes cnt particles per tile directly
       ZP_CU(cudaMemcpyAsync(P.cnt.p, cnt.data(), sizeof(int) * S.ntiles,
                             cudaMemcpyHostToDevice, stream_));
@@ -997,8 +999,16 @@ class Batch : public BatchBase {
   }
 
   // Allocates the tile store of species s for per-tile counts cnt.
-  static int full_tile_cap(double nominal, double slack) {
-    return std::max(64, (int)std::ceil(nominal * (1.0 + slack)));
+  // Room every tile of a species gets: its full density plus the slack; a
+  // plasma that flows through a moving window is compressed as it passes
+  // the laser (wake, channel walls), so its tiles get room for twice their
+  // full density.
+  static int full_tile_cap(double nominal, double slack, bool window_plasma) {
+    const double f = window_plasma ? std::max(1.0 + slack, 2.0) : 1.0 + slack;
+    return std::max(64, (int)std::ceil(nominal * f));
+  }
+  static bool window_plasma(const SimHost<R> &S, const SpeciesHost<R> &P) {
+    return S.cfg.moving_window && P.cfg.profile != ZPIC_PROFILE_NONE;
   }
 
   // Capacity of tile t: room for its count plus the slack, and at least
@@ -1007,19 +1017,39 @@ class Batch : public BatchBase {
   // window injecting plasma) without a re-sort; only compression beyond
   // that density overflows.
   int alloc_store(int si, int s, const std::vector<int> &cnt, double slack,
-                  int min_cap) {
+                  double nominal, int min_cap) {
     SimHost<R> &S = sims_[si];
     SpeciesHost<R> &P = S.sp[s];
     std::vector<int> off(S.ntiles), cap(S.ntiles);
+    // densest tile within two tiles of each tile (a compressed structure
+    // moving through the tiles reaches its neighbours next)
+    std::vector<int> near(S.ntiles, 0);
+    for (int t = 0; t < S.ntiles; ++t) {
+      const int tx = t % S.ntx, ty = t / S.ntx;
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          const int x = tx + dx, y = (ty + dy + S.nty) % S.nty;
+          if (x < 0 || x >= S.ntx) continue;
+          near[t] = std::max(near[t], cnt[y * S.ntx + x]);
+        }
+    }
     long long tot = 0;
     for (int t = 0; t < S.ntiles; ++t) {
       long long c = std::max<long long>((long long)std::ceil(cnt[t] * (1.0 + slack)),
                                         (long long)cnt[t] + 64);
       c = std::max<long long>(c, min_cap);
-      // a tile that outgrew its capacity at least doubles it, so a tile that
-      // keeps filling (a moving front) needs few re-sorts
-      if (!P.h_cap.empty() && cnt[t] > P.h_cap[t])
-        c = std::max<long long>(c, 2LL * P.h_cap[t]);
+      // a tile keeps the capacity it had (density structures such as a
+      // laser wake stay in the same tiles and come back after a dip), and a
+      // tile that outgrew its capacity at least doubles it, so a tile that
+      // keeps filling needs few re-sorts
+      if (!P.h_cap.empty()) {
+        c = std::max<long long>(c, P.h_cap[t]);
+        if (cnt[t] > P.h_cap[t]) c = std::max<long long>(c, 2LL * P.h_cap[t]);
+      }
+      // a tile near one denser than the species' full density may be
+      // compressed next (a wake, a filament, a channel wall moving through
+      // the tiles): room for twice that density before it overflows
+      if (near[t] > nominal) c = std::max<long long>(c, 2LL * near[t]);
       c = (c + 31) / 32 * 32;
       if (tot + c > INT_MAX) return fail(ZPIC_ENOMEM, "species store exceeds 2^31");
       off[t] = (int)tot;
@@ -1046,6 +1076,8 @@ class Batch : public BatchBase {
           !dalloc(P.cnt, 4 * S.ntiles) || !dalloc(P.ob_cnt, 4 * S.ntiles))
         return fail(ZPIC_ENOMEM, "tile tables");
       ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
+    }
+    if (!P.ob_ix.p) {  // outbox planes (again after the outbox grew)
       const size_t nob = (size_t)P.ob_cap * S.ntiles;
       if (!dalloc(P.ob_ix, 4 * nob) || !dalloc(P.ob_iy, 4 * nob) ||
           !dalloc(P.ob_x, sizeof(R) * nob) || !dalloc(P.ob_y, sizeof(R) * nob) ||
@@ -1297,7 +1329,8 @@ class Batch : public BatchBase {
       return fail(ZPIC_EINVAL, "particles outside the grid or offsets not in [0,1)");
     const double slack = S.cfg.capacity_slack > 0 ? S.cfg.capacity_slack : 0.25;
     const double nominal = (double)P.cfg.ppc_x * P.cfg.ppc_y * S.tx * S.ty;
-    ZP_TRY(alloc_store(si, s, cnt, slack, full_tile_cap(nominal, slack)));
+    ZP_TRY(alloc_store(si, s, cnt, slack, nominal,
+                       full_tile_cap(nominal, slack, window_plasma(S, P))));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1, S.tx,
@@ -1321,6 +1354,30 @@ class Batch : public BatchBase {
 
   // After ERR_OVERFLOW: every species of every sim with parked particles is
   // compacted, joined with its overflow entries and re-binned with more room.
+  // A tile had more leavers in one step than its outbox holds (the excess
+  // went to the overflow buffer): give every tile of the species an outbox
+  // of twice that many (the planes are allocated again by alloc_store).
+  int grow_outbox(int si, int s) {
+    SimHost<R> &S = sims_[si];
+    SpeciesHost<R> &P = S.sp[s];
+    int need = 0;
+    ZP_CU(cudaMemcpy(&need, S.dev.ob_need + s, sizeof(int),
+                     cudaMemcpyDeviceToHost));
+    if (need <= P.ob_cap) return ZPIC_OK;
+    const long long cap = ((2LL * need + 31) / 32) * 32;
+    if (cap * S.ntiles >= INT_MAX)
+      return fail(ZPIC_EOVERFLOW, "outbox index range exceeded");
+    for (DevMem *m : {&P.ob_ix, &P.ob_iy, &P.ob_x, &P.ob_y, &P.ob_ux,
+                      &P.ob_uy, &P.ob_uz, &P.ob_w, &P.ob_id})
+      dfree(*m);
+    P.ob_cap = (int)cap;
+    S.dev.sp[s].ob_cap = (int)cap;
+    const int zero = 0;
+    ZP_CU(cudaMemcpy(S.dev.ob_need + s, &zero, sizeof(int),
+                     cudaMemcpyHostToDevice));
+    return ZPIC_OK;
+  }
+
   int resort_all() {
     NvtxRange r_("zpic re-sort after tile overflow");
     const int n_ovf = std::min(h_st_->ovf_count, ovf_cap_);
@@ -1353,6 +1410,7 @@ class Batch : public BatchBase {
         ZP_CU(launch_take_overflow<R>(ovf_, n_ovf, si, s, stg_, n,
                                       (int *)bad_.p, stream_));
         ZP_CU(cudaStreamSynchronize(stream_));
+        ZP_TRY(grow_outbox(si, s));
         // copies of the compacted store are in staging now; rebuild
         ZP_TRY(rebuild_species(si, s, n + extra, S.sp[s].has_w,
                                S.sp[s].has_id, false));

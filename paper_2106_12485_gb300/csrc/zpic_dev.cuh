@@ -117,6 +117,9 @@ struct SimDev {
   int *hist_n;                 // records written
   int *n_shift;                // window shifts done
   int *removed;                // [kMaxSpecies] particles removed at edges
+  int *ob_need;                // [kMaxSpecies] most leavers one tile had in
+                               // a step when that exceeded its outbox
+                               // (0: none); the re-sort grows the outbox
   SpeciesDev<R> sp[kMaxSpecies];
 };
 
