@@ -57,7 +57,7 @@ def parse_args():
                     help="cells per side of the oracle sample")
     ap.add_argument("--workload", default="uniform",
                     choices=["uniform", "clouds", "lwfa", "lwfa_paper",
-                             "weibel", "batch", "precision"],
+                             "weibel", "batch", "precision", "tiles"],
                     help="uniform (default): the large uniform plasma; the "
                     "others print one line for that workload")
     return ap.parse_args()
@@ -361,6 +361,21 @@ def other_workload(args):
              "steps_before_timing": warm},
             resorts_in_timed_region=info.resorts - r0,
             step_after=int(info.step))))
+        return
+    if args.workload == "tiles":
+        # the autotuner's tile-size sweep for the workload classes (each on
+        # its copy reduced to at most 1024 x 1024 cells)
+        out = {}
+        for name, cfg in (("uniform_2048", W.precision_study()),
+                          ("clouds_1024", W.clouds()),
+                          ("lwfa_4096x512", W.lwfa()),
+                          ("weibel_512", W.weibel())):
+            bx, by, times = Z.autotune(cfg, steps=args.steps)
+            out[name] = {"best": [bx, by],
+                         "ms_per_step": {"%dx%d" % k: round(v, 4)
+                                         for k, v in times.items()}}
+        print(json.dumps({"workload": "tile-size sweep (autotuner)",
+                          "steps": args.steps, "classes": out}))
         return
     if args.workload == "batch":
         specs = P.batch_specs(256)

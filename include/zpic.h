@@ -143,7 +143,9 @@ typedef struct {
     uint64_t seed;              /* generator seed of the initial load     */
     int sim_index;              /* generator stream of this simulation    */
     int energy_every;           /* record energies every k steps; 0: off  */
-    int tile_x, tile_y;         /* tile size in cells, 2..32; 0: 16       */
+    int tile_x, tile_y;         /* tile size in cells, 2..32; 0: the size
+                                   zpic_autotune chose for this
+                                   configuration's class, else 16         */
     int flags;                  /* ZPIC_TRACK_IDS | ZPIC_FILTER_J         */
     double capacity_slack;      /* spare tile capacity fraction; 0: 0.25  */
 } zpic_config;
@@ -331,6 +333,28 @@ int zpic_set_state(zpic_sim *sim, const zpic_state *in);
 int zpic_phasespace(zpic_sim *sim, int species, int qx, int qy,
                     const double range[4], int nbx, int nby, double *dst,
                     size_t cap);
+
+/* Tile-size autotuner (host).  Times the step of cfg for each candidate
+ * tile size (zpic_autotune_candidates lists them as x, y pairs) on a copy
+ * reduced to at most 1024 x 1024 cells (same cell size, dt, species,
+ * densities and momenta; slab profiles scaled with the box; a ramp, the
+ * window plasma and the laser kept at the same distance from the right
+ * edge), `steps` steps after 3 warm-up steps, host wall clock, and returns
+ * the fastest in *best_tile_x, *best_tile_y.  The choice is kept for the
+ * configuration's class (precision, reduced grid, boundary, window, filter,
+ * particles per cell and profile of each species) for the life of the
+ * process; zpic_create uses it when tile_x = tile_y = 0.  With
+ * ms_per_step == NULL a class already tuned returns at once; otherwise the
+ * candidates are timed and ms_per_step[k] (k < cap) receives candidate k's
+ * ms per step (negative: the candidate could not run).  Errors:
+ * ZPIC_EINVAL (NULL cfg or result, steps outside [1, 10000]), the errors of
+ * zpic_create for cfg, ZPIC_ECUDA when no candidate ran. */
+int zpic_autotune(const zpic_config *cfg, int steps, int *best_tile_x,
+                  int *best_tile_y, double *ms_per_step, int cap,
+                  int *n_candidates);
+/* Writes up to cap candidate tile sizes (x, y pairs) to tile_xy and returns
+ * how many candidates there are. */
+int zpic_autotune_candidates(int *tile_xy, int cap);
 
 /* Kernel timing: when enabled, zpic_step launches kernels one by one and
  * records a CUDA event pair around each launch on the handle's stream.

@@ -1,0 +1,172 @@
+// autotune.cu -- host autotuner of the particle tile size.
+//
+// The tile is the unit of work of the push (one CTA per tile) and of the
+// particle sort, so its size trades shared-memory staging and guard-cell
+// overhead (small tiles) against CTA count and load balance (large tiles,
+// few particles). zpic_autotune times one configuration for each candidate
+// tile size on a copy reduced to at most 1024 x 1024 cells (same cell size,
+// time step, species, densities and momenta; profiles, window and laser
+// placed at the same distance from the right edge), keeps the fastest per
+// configuration class, and zpic_create uses that choice when a
+// configuration asks for tile size 0 (default 16 x 16 otherwise).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/zpic.h"
+
+namespace zp {
+int set_last_error(int code, const char *msg);
+}
+
+namespace {
+
+// Side of the reduced copy: large enough that every candidate gives many
+// waves of CTAs (at 256 x 256 the GPU is under-filled by 16 x 16 tiles and
+// smaller tiles win for that reason alone; measured on the 2048^2 plasma:
+// 16 x 16 is fastest at full size, 12 x 12 on a 256^2 copy).
+constexpr int kMaxSide = 1024;
+
+std::mutex g_mu;
+std::map<std::string, std::pair<int, int>> g_tuned;
+
+// The class of a configuration: what decides the best tile size is the
+// precision, the particles per cell of each species (the work per tile),
+// the boundary and window, the current filter and the reduced grid shape.
+std::string class_key(const zpic_config &c) {
+  std::string k = "p" + std::to_string(c.precision) + " n" +
+                  std::to_string(std::min(c.nx, kMaxSide)) + "x" +
+                  std::to_string(std::min(c.ny, kMaxSide)) + " b" +
+                  std::to_string(c.bc_x) + " w" +
+                  std::to_string(c.moving_window) + " f" +
+                  std::to_string(c.flags & ZPIC_FILTER_J);
+  for (int s = 0; s < c.n_species; ++s)
+    k += " s" + std::to_string(c.species[s].ppc_x * c.species[s].ppc_y) + ":" +
+         std::to_string(c.species[s].profile);
+  return k;
+}
+
+zpic_config reduced(const zpic_config &c) {
+  zpic_config r = c;
+  const double dx = c.box_x / c.nx, dy = c.box_y / c.ny;
+  r.nx = std::min(c.nx, kMaxSide);
+  r.ny = std::min(c.ny, kMaxSide);
+  r.box_x = r.nx * dx;
+  r.box_y = r.ny * dy;
+  const double fx = r.box_x / c.box_x;
+  for (int s = 0; s < c.n_species; ++s) {
+    zpic_species &p = r.species[s];
+    if (p.profile == ZPIC_PROFILE_SLAB) {
+      p.x0 = c.species[s].x0 * fx;
+      p.x1 = c.species[s].x1 * fx;
+    } else if (p.profile == ZPIC_PROFILE_RAMP) {
+      p.x0 = r.box_x - (c.box_x - c.species[s].x0);  // same gap to the edge
+    }
+  }
+  if (c.laser.enabled) {
+    r.laser.x0 = r.box_x - (c.box_x - c.laser.x0);
+    r.laser.y_center = c.laser.y_center * r.box_y / c.box_y;
+  }
+  r.energy_every = 0;
+  r.flags &= ~ZPIC_TRACK_IDS;
+  return r;
+}
+
+// Host wall time of `steps` steps after a warm-up (ms per step), or a
+// negative value if the candidate cannot run (e.g. too large for shared
+// memory).
+double time_candidate(const zpic_config &r, int steps) {
+  zpic_sim *h = nullptr;
+  if (zpic_create(&r, &h) != ZPIC_OK) return -1.0;
+  double ms = -1.0;
+  if (zpic_step(h, 3) == ZPIC_OK && zpic_sync(h) == ZPIC_OK) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (zpic_step(h, steps) == ZPIC_OK && zpic_sync(h) == ZPIC_OK) {
+      const auto t1 = std::chrono::steady_clock::now();
+      ms = std::chrono::duration<double, std::milli>(t1 - t0).count() / steps;
+    }
+  }
+  zpic_destroy(h);
+  return ms;
+}
+
+const int kCand[][2] = {{16, 16}, {8, 8}, {12, 12}, {24, 24}, {32, 32},
+                        {32, 16}, {16, 32}};
+constexpr int kNCand = sizeof(kCand) / sizeof(kCand[0]);
+
+}  // namespace
+
+namespace zp {
+// The tuned tile size of c's class, if zpic_autotune has run for it.
+bool tuned_tile(const zpic_config &c, int *tx, int *ty) {
+  std::lock_guard<std::mutex> g(g_mu);
+  auto it = g_tuned.find(class_key(c));
+  if (it == g_tuned.end()) return false;
+  *tx = it->second.first;
+  *ty = it->second.second;
+  return true;
+}
+}  // namespace zp
+
+extern "C" {
+
+int zpic_autotune(const zpic_config *cfg, int steps, int *best_tile_x,
+                  int *best_tile_y, double *ms_per_step, int cap,
+                  int *n_candidates) {
+  if (!cfg || !best_tile_x || !best_tile_y)
+    return zp::set_last_error(ZPIC_EINVAL, "NULL argument");
+  if (steps < 1 || steps > 10000)
+    return zp::set_last_error(ZPIC_EINVAL, "steps out of range");
+  if (n_candidates) *n_candidates = kNCand;
+  const std::string key = class_key(*cfg);
+  if (!ms_per_step) {
+    std::lock_guard<std::mutex> g(g_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      *best_tile_x = it->second.first;
+      *best_tile_y = it->second.second;
+      return ZPIC_OK;
+    }
+  }
+  double best = -1.0;
+  int bx = 16, by = 16;
+  int status = ZPIC_OK;
+  for (int k = 0; k < kNCand; ++k) {
+    zpic_config r = reduced(*cfg);
+    r.tile_x = kCand[k][0];
+    r.tile_y = kCand[k][1];
+    const double ms = time_candidate(r, steps);
+    if (ms_per_step && k < cap) ms_per_step[k] = ms;
+    if (ms > 0 && (best < 0 || ms < best)) {
+      best = ms;
+      bx = kCand[k][0];
+      by = kCand[k][1];
+    }
+  }
+  if (best < 0)
+    return zp::set_last_error(ZPIC_ECUDA, "no tile size candidate could run");
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    g_tuned[key] = {bx, by};
+  }
+  *best_tile_x = bx;
+  *best_tile_y = by;
+  return status;
+}
+
+int zpic_autotune_candidates(int *tile_xy, int cap) {
+  if (!tile_xy && cap > 0) return zp::set_last_error(ZPIC_EINVAL, "NULL buffer");
+  for (int k = 0; k < kNCand && k < cap; ++k) {
+    tile_xy[2 * k] = kCand[k][0];
+    tile_xy[2 * k + 1] = kCand[k][1];
+  }
+  return kNCand;
+}
+
+}  // extern "C"

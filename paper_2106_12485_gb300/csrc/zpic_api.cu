@@ -43,6 +43,7 @@ static int fail(int code, const std::string &msg) {
 namespace zp {
 // error reporting for the ABI entry points defined in other files
 int set_last_error(int code, const char *msg) { return fail(code, msg); }
+bool tuned_tile(const zpic_config &c, int *tx, int *ty);  // autotune.cu
 }  // namespace zp
 
 static int cuda_fail(cudaError_t e, const char *what) {
@@ -837,8 +838,10 @@ class Batch : public BatchBase {
     S.dx = c.box_x / c.nx;
     S.dy = c.box_y / c.ny;
     S.dt = c.dt;
-    S.tx = std::min(c.tile_x ? c.tile_x : 16, c.nx);
-    S.ty = std::min(c.tile_y ? c.tile_y : 16, c.ny);
+    int tx = c.tile_x, ty = c.tile_y;
+    if (tx == 0 && ty == 0 && !tuned_tile(c, &tx, &ty)) tx = ty = 16;
+    S.tx = std::min(tx ? tx : 16, c.nx);
+    S.ty = std::min(ty ? ty : 16, c.ny);
     if (push_smem_bytes<R>(S.tx, S.ty, true) > 226 * 1024)
       return fail(ZPIC_EINVAL, "tile too large for shared memory");
     S.ntx = (S.nx + S.tx - 1) / S.tx;

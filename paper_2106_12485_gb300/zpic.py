@@ -118,6 +118,10 @@ _PROTOS = {
     "zpic_set_state": (C.c_int, [_P, C.POINTER(zpic_state)]),
     "zpic_phasespace": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int,
                                   C.c_int, _P, C.c_size_t]),
+    "zpic_autotune": (C.c_int, [C.POINTER(zpic_config), C.c_int,
+                                C.POINTER(C.c_int), C.POINTER(C.c_int), _P,
+                                C.c_int, C.POINTER(C.c_int)]),
+    "zpic_autotune_candidates": (C.c_int, [_P, C.c_int]),
     "zpic_profile_enable": (C.c_int, [_P, C.c_int]),
     "zpic_profile_read": (C.c_int, [_P, _P, C.c_size_t, _P, _P, C.c_int,
                                     C.POINTER(C.c_int), C.c_int]),
@@ -416,6 +420,23 @@ class Sim:
             nm = names.raw[k * nl:(k + 1) * nl].split(b"\0")[0].decode()
             out[nm] = (float(ms[k]), int(la[k]))
         return out
+
+
+def autotune(cfg, steps=10, retune=True):
+    """Best tile size for cfg's class: (tile_x, tile_y, {(tx, ty): ms per
+    step}) with every candidate timed (retune=True), or the cached choice
+    with an empty dict (retune=False, after an earlier tuning)."""
+    n = lib().zpic_autotune_candidates(None, 0)
+    xy = np.zeros(2 * n, np.int32)
+    lib().zpic_autotune_candidates(_ptr(xy), n)
+    ms = np.zeros(n)
+    bx, by, nc = C.c_int(), C.c_int(), C.c_int()
+    check(lib().zpic_autotune(C.byref(cfg), steps, C.byref(bx), C.byref(by),
+                              _ptr(ms) if retune else None, n, C.byref(nc)),
+          "zpic_autotune")
+    times = {(int(xy[2 * k]), int(xy[2 * k + 1])): float(ms[k])
+             for k in range(n)} if retune else {}
+    return bx.value, by.value, times
 
 
 def load_checkpoint(cfg, path):
