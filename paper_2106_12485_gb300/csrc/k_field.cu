@@ -18,8 +18,10 @@
 
 namespace zp {
 
-// periodic index for any i (the 34 x 10 halo can exceed twice a tiny grid)
+// periodic index for any i (the 34 x 10 halo can exceed twice a tiny grid);
+// indices already in range, nearly all of them, skip the division
 __device__ __forceinline__ int wrapg(int i, int n) {
+  if ((unsigned)i < (unsigned)n) return i;
   i %= n;
   return i < 0 ? i + n : i;
 }
