@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(kThreads)
     const int t = atomicAdd(&st->blocks_done, 1);
     if (t == (int)gridDim.x - 1) {
       st->blocks_done = 0;
+      st->push_next = 0;  // the next step's push takes items from 0
       __threadfence();
       st->step = step + 1;
     }

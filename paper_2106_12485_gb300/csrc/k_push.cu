@@ -846,34 +846,46 @@ template <typename R, bool kBatch, int TXC, int TYC>
 __global__ void __launch_bounds__(kPT, sizeof(R) == 4 ? kPushCtasF32 : 2)
     push_deposit_kernel(const SimDev<R> *__restrict__ sims,
                         const __grid_constant__ SimDev<R> one,
-                        const int2 *__restrict__ items, BatchStatus *st,
+                        const int2 *__restrict__ items, int n_items,
+                        BatchStatus *st,
                         const __grid_constant__ OverflowDev<R> ovf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slots[2];  // stayers written, leavers written
   __shared__ double red[kPW];
+  __shared__ int s_item;
 
   const int step = st->step;
   if (frozen(st, step)) return;
-  const int2 it = items[blockIdx.x];
-  const SimDev<R> &S = kBatch ? sims[it.x] : one;
-  // a tile without particles deposits nothing and loses nothing: it only
-  // reports empty outboxes (and zero kinetic energy on energy steps)
-  int n_all = 0;
-  for (int s = 0; s < S.nsp; ++s) n_all += S.sp[s].cnt[it.y];
-  if (n_all == 0) {
-    if (threadIdx.x < S.nsp) {
-      S.sp[threadIdx.x].ob_cnt[it.y] = 0;
-      if (S.energy_every > 0 && ((step + 1) % S.energy_every) == 0)
-        S.part_kin[(size_t)it.y * kMaxSpecies + threadIdx.x] = 0.0;
+  // persistent: as many CTAs as fit on the GPU take the work items (tiles,
+  // longest first) from a counter that the end-of-step kernel resets
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&st->push_next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= n_items) return;
+    const int2 it = items[item];
+    const SimDev<R> &S = kBatch ? sims[it.x] : one;
+    // a tile without particles deposits nothing and loses nothing: it only
+    // reports empty outboxes (and zero kinetic energy on energy steps)
+    int n_all = 0;
+    for (int s = 0; s < S.nsp; ++s) n_all += S.sp[s].cnt[it.y];
+    if (n_all == 0) {
+      if (threadIdx.x < S.nsp) {
+        S.sp[threadIdx.x].ob_cnt[it.y] = 0;
+        if (S.energy_every > 0 && ((step + 1) % S.energy_every) == 0)
+          S.part_kin[(size_t)it.y * kMaxSpecies + threadIdx.x] = 0.0;
+      }
+      continue;
     }
-    return;
+    if (step & 1)
+      push_tile<R, kBatch, TXC, TYC, 1>(S, it.x, it.y, step, st, ovf,
+                                        smem_raw, s_slots, red);
+    else
+      push_tile<R, kBatch, TXC, TYC, 0>(S, it.x, it.y, step, st, ovf,
+                                        smem_raw, s_slots, red);
+    __syncthreads();  // shared memory is reused by the next item
   }
-  if (step & 1)
-    push_tile<R, kBatch, TXC, TYC, 1>(S, it.x, it.y, step, st, ovf, smem_raw,
-                                      s_slots, red);
-  else
-    push_tile<R, kBatch, TXC, TYC, 0>(S, it.x, it.y, step, st, ovf, smem_raw,
-                                      s_slots, red);
 }
 
 template <typename R>
@@ -899,6 +911,21 @@ cudaError_t prepare_push_deposit(int max_tx, int max_ty, bool wide) {
   return set_push_smem<R, true>(smem);
 }
 
+// Resident CTAs of kernel k per SM for `smem` bytes of dynamic shared
+// memory, times the SM count: the grid of the persistent push kernel.
+template <typename K>
+static int persistent_grid(K kernel, size_t smem, int n_items) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPT,
+                                                    smem) != cudaSuccess ||
+      per_sm < 1)
+    return n_items;
+  return n_items < sms * per_sm ? n_items : sms * per_sm;
+}
+
 template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
@@ -911,19 +938,25 @@ cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
   // tiles (ragged edge tiles are fine)
   const bool t16 = all16;
   if (single) {
-    if (t16)
-      push_deposit_kernel<R, false, 16, 16><<<n_items, kPT, smem, stream>>>(
-          sims, *single, items, st, ovf);
-    else
-      push_deposit_kernel<R, false, 0, 0><<<n_items, kPT, smem, stream>>>(
-          sims, *single, items, st, ovf);
+    if (t16) {
+      auto k = push_deposit_kernel<R, false, 16, 16>;
+      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+          sims, *single, items, n_items, st, ovf);
+    } else {
+      auto k = push_deposit_kernel<R, false, 0, 0>;
+      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+          sims, *single, items, n_items, st, ovf);
+    }
   } else {
-    if (t16)
-      push_deposit_kernel<R, true, 16, 16><<<n_items, kPT, smem, stream>>>(
-          sims, SimDev<R>{}, items, st, ovf);
-    else
-      push_deposit_kernel<R, true, 0, 0><<<n_items, kPT, smem, stream>>>(
-          sims, SimDev<R>{}, items, st, ovf);
+    if (t16) {
+      auto k = push_deposit_kernel<R, true, 16, 16>;
+      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+          sims, SimDev<R>{}, items, n_items, st, ovf);
+    } else {
+      auto k = push_deposit_kernel<R, true, 0, 0>;
+      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+          sims, SimDev<R>{}, items, n_items, st, ovf);
+    }
   }
   return cudaGetLastError();
 }

@@ -44,7 +44,8 @@ struct BatchStatus {
   int ovf_count;    // entries claimed in the overflow buffer
   int lost;         // particles dropped (overflow buffer full)
   int blocks_done;  // ticket counter of the end-of-step kernel
-  int pad[2];
+  int push_next;    // next work item of the persistent push kernel
+  int pad;
 };
 
 // One copy of a species' tile store: SoA planes (w, id may be null).  The
