@@ -1,26 +1,31 @@
 // k_push.cu -- fused particle kernel: interpolation, Boris push, move,
 // charge-conserving deposition and in-tile compaction (PIC stages 1-3 of
 // Sec. 2.2; the per-region particle advance with local current buffers and
-// a ghost-cell reduction of Sec. 3.2, here one CTA per tile).
+// a ghost-cell reduction of Sec. 3.2, here one CTA per tile at a time).
 //
-// Per work item (simulation, tile) one CTA:
-//  1. stages E, B of the tile plus one guard cell on each side in shared
-//     memory ([-1, tx] x [-1, ty]) and zeroes a shared J tile covering
+// Persistent: the resident CTAs take (simulation, tile) items, longest
+// first, from a device counter.  Per item the CTA
+//  1. stages E, B of the tile plus one guard cell on each side and turns
+//     them into a coefficient tile (the bilinear interpolant of every cell
+//     of every staggered component), and zeroes a shared J tile covering
 //     [-1, tx+1] x [-1, ty+1];
-//  2. streams the tile's particles in chunks of 32 per warp: bilinear
-//     gather of the staggered fields from shared memory, relativistic Boris
+//  2. streams the tile's particles in chunks of 32 per warp, the next
+//     chunk's records arriving through a per-warp ring of asynchronous
+//     copies: bilinear gather from the coefficient tile, relativistic Boris
 //     rotation, move by dt u/gamma (at most one cell, CFL), split of the
 //     straight path at the cell faces it crosses; the segment in the start
-//     cell goes straight into the shared J tile, the segments of particles
-//     that cross a face wait in a per-warp queue and are deposited 32 at a
-//     time;
+//     cell goes straight into the shared J tile (exact fixed point), the
+//     paths of particles that cross a face wait in a per-warp queue and
+//     their remaining segments are deposited 32 at a time;
 //  3. writes particles that stay in the tile to the tile's segment of the
 //     other copy of the store (each warp claims a run of slots with one
 //     shared-memory atomic, so warps never wait for each other) and
 //     particles that leave to the tile's outbox; particles leaving an open
 //     boundary are dropped;
-//  4. adds the shared J tile (interior and guard cells) to the global J
-//     with one reduction per cell (periodic images folded here).
+//  4. adds the shared J tile (interior and guard cells) to the global J,
+//     one reduction per cell (periodic images folded here); in FP32 the
+//     global J is an int64 fixed-point sum, so the result does not depend
+//     on the order of the tiles.
 // Traffic per particle: one read and one write of its SoA record (16-bit
 // cell within the tile + 5 reals: 22 bytes in FP32).
 #include <type_traits>
