@@ -287,18 +287,36 @@ __global__ void __launch_bounds__(kThreads)
   if (do_energy) {
     const int ntiles = S.ntx * S.nty;
     double kin[kMaxSpecies];
+    // four independent partial sums per thread keep four loads in flight;
+    // they are combined in a fixed order, so the total is reproducible
+    const int T4 = 4 * blockDim.x;
     for (int s = 0; s < S.nsp; ++s) {
-      double v = 0.0;
-      for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-        v += S.part_kin[(size_t)t * kMaxSpecies + s];
-      kin[s] = block_sum(v, red) * S.sp[s].kin_scale;
+      const double *pk = S.part_kin + (size_t)s * ntiles;
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int t = threadIdx.x;
+      for (; t + 3 * (int)blockDim.x < ntiles; t += T4) {
+        v0 += pk[t];
+        v1 += pk[t + blockDim.x];
+        v2 += pk[t + 2 * blockDim.x];
+        v3 += pk[t + 3 * blockDim.x];
+      }
+      for (; t < ntiles; t += blockDim.x) v0 += pk[t];
+      kin[s] = block_sum((v0 + v1) + (v2 + v3), red) * S.sp[s].kin_scale;
     }
     const int nyb = S.ybx * S.yby;
-    double e = 0.0, b = 0.0;
-    for (int t = threadIdx.x; t < nyb; t += blockDim.x) {
-      e += S.part_fld[2 * (size_t)t];
-      b += S.part_fld[2 * (size_t)t + 1];
+    double e0 = 0.0, e1 = 0.0, b0 = 0.0, b1 = 0.0;
+    int t = threadIdx.x;
+    for (; t + (int)blockDim.x < nyb; t += 2 * blockDim.x) {
+      e0 += S.part_fld[2 * (size_t)t];
+      b0 += S.part_fld[2 * (size_t)t + 1];
+      e1 += S.part_fld[2 * (size_t)(t + blockDim.x)];
+      b1 += S.part_fld[2 * (size_t)(t + blockDim.x) + 1];
     }
+    for (; t < nyb; t += blockDim.x) {
+      e0 += S.part_fld[2 * (size_t)t];
+      b0 += S.part_fld[2 * (size_t)t + 1];
+    }
+    double e = e0 + e1, b = b0 + b1;
     e = block_sum(e, red);
     b = block_sum(b, red);
     if (threadIdx.x == 0) {

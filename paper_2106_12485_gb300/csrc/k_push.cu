@@ -700,7 +700,7 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   if (n_removed) atomicAdd(&S.removed[s], n_removed);
   if (T.do_energy)
     block_sum_store<R>((double)kin,
-                       &S.part_kin[(size_t)T.tile * kMaxSpecies + s], T.red);
+                       &S.part_kin[(size_t)s * S.ntx * S.nty + T.tile], T.red);
   __syncthreads();
   if (threadIdx.x == 0) {
     P.cnt[T.tile] = T.s_slots[0];
@@ -879,7 +879,7 @@ __global__ void __launch_bounds__(kPT, sizeof(R) == 4 ? kPushCtasF32 : 2)
       if (threadIdx.x < S.nsp) {
         S.sp[threadIdx.x].ob_cnt[it.y] = 0;
         if (S.energy_every > 0 && ((step + 1) % S.energy_every) == 0)
-          S.part_kin[(size_t)it.y * kMaxSpecies + threadIdx.x] = 0.0;
+          S.part_kin[(size_t)threadIdx.x * S.ntx * S.nty + it.y] = 0.0;
       }
       continue;
     }

@@ -109,7 +109,7 @@ struct SimDev {
   // contributes at most one unit) and add it to Jq; jscale converts a sum
   // to J.
   double jscale[3];
-  double *part_kin;            // [ntiles][kMaxSpecies] kinetic partials
+  double *part_kin;            // [kMaxSpecies][ntiles] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
   zpic_energy_rec *hist;       // energy history
   int hist_cap;
