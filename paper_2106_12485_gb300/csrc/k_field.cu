@@ -13,6 +13,8 @@
 // cell: read E, B, J (9 values), write E, B (6) and zero the other J (3).
 #include <math.h>
 
+#include <type_traits>
+
 #include "zpic_dev.cuh"
 #include "zpic_kernels.h"
 
@@ -51,6 +53,28 @@ __device__ __forceinline__ R fld_j(const SimDev<R> &S, int cur, int c, int gi,
   return j_value(S, cur, c, (size_t)gj * S.ld + gi);
 }
 
+// The deposited current as stored (FP32: the int64 fixed-point sum; FP64:
+// the double), for loads that are scaled only once they have all arrived.
+template <typename R>
+using JRaw = typename std::conditional<sizeof(R) == 4, long long, R>::type;
+
+template <typename R>
+__device__ __forceinline__ const JRaw<R> *j_plane(const SimDev<R> &S, int cur,
+                                                  int c) {
+  if constexpr (sizeof(R) == 4)
+    return S.Jq[cur][c];
+  else
+    return S.J[cur][c];
+}
+
+template <typename R>
+__device__ __forceinline__ R j_scale(const SimDev<R> &S, int c, JRaw<R> v) {
+  if constexpr (sizeof(R) == 4)
+    return fixed_to_float(v) * S.jscale[c];
+  else
+    return v;
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -60,6 +84,34 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;  // valid in warp 0 lane 0 (and every warp's lane 0)
+}
+
+// Sums (e, b) over the CTA and stores the two totals at dst[0], dst[1]:
+// each warp adds its 32 values in R (the cells' squares are R already),
+// thread 0 adds the warp sums in double, in warp order.  Keeps the FP64 work
+// of the field-energy report at one add per warp.
+template <typename R>
+__device__ __forceinline__ void block_sum2_store(R e, R b, double *red,
+                                                 double *dst) {
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[2 * warp] = (double)e;
+    red[2 * warp + 1] = (double)b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double se = 0.0, sb = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      se += red[2 * w];
+      sb += red[2 * w + 1];
+    }
+    dst[0] = se;
+    dst[1] = sb;
+  }
 }
 
 template <typename R>
@@ -73,7 +125,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ R se[3][EH][EW];
   __shared__ R sb[3][BH][BW];
   __shared__ R sj[3][JH][JW];
-  __shared__ double red[kWarps];
+  __shared__ double red[2 * kWarps];
 
   const int step = st->step;
   if (frozen(st, step)) return;
@@ -82,31 +134,107 @@ __global__ void __launch_bounds__(kThreads)
   const int bx = it.y % S.ybx, by = it.y / S.ybx;
   const int x0 = bx * X, y0 = by * Y;
   const int cur = step & 1, nxt = cur ^ 1;
-  const int shift = shift_due(S, step, S.moving_window ? *S.n_shift : 0);
+  // the window decision (FP64) once per block, read after the first barrier
+  __shared__ int s_shift;
+  if (threadIdx.x == 0)
+    s_shift = shift_due(S, step, S.moving_window ? *S.n_shift : 0);
   const bool do_energy =
       S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
   const R dt = S.dt, h = R(0.5) * S.dt;
   const R rdx = R(1) / S.dx, rdy = R(1) / S.dy;
 
-  for (int k = threadIdx.x; k < 3 * EH * EW; k += blockDim.x) {
-    const int c = k / (EH * EW), r = k - c * (EH * EW);
-    const int lj = r / EW, li = r - lj * EW;
-    se[c][lj][li] = fld(S, S.E[cur][c], x0 - 1 + li, y0 - 1 + lj);
+  // The block's halo, cells [x0-1, x0+X+2) x [y0-1, y0+Y+2): E uses all of
+  // it, B the first BW x BH, J the part from (x0, y0) on.  Each thread takes
+  // halo cells k = tid + u kThreads, works out the cell's address once for
+  // all nine arrays, and issues every load before its first shared-memory
+  // store, so a block waits for one memory round trip.
+  constexpr int HN = EH * EW;
+  constexpr int UH = (HN + kThreads - 1) / kThreads;
+  const bool filtered = S.Jf[0] != nullptr;  // drive E with the filtered J
+  const int nx = S.nx, ny = S.ny;
+  const bool open_x = S.open_x != 0;
+  size_t off[UH];
+  bool in[UH];   // inside the halo and not beyond an open x edge
+  int hl[UH];    // (lj << 8) | li
+#pragma unroll
+  for (int u = 0; u < UH; ++u) {
+    const int k = threadIdx.x + u * kThreads;
+    const int lj = k / EW, li = k - lj * EW;
+    int gi = x0 - 1 + li;
+    const int gj = wrapg(y0 - 1 + lj, ny);
+    bool ok = k < HN;
+    if (open_x)
+      ok = ok && gi >= 0 && gi < nx;
+    else
+      gi = wrapg(gi, nx);
+    in[u] = ok;
+    off[u] = (size_t)gj * S.ld + (ok ? gi : 0);
+    hl[u] = (lj << 8) | li;
   }
-  for (int k = threadIdx.x; k < 3 * BH * BW; k += blockDim.x) {
-    const int c = k / (BH * BW), r = k - c * (BH * BW);
-    const int lj = r / BW, li = r - lj * BW;
-    sb[c][lj][li] = fld(S, S.B[cur][c], x0 - 1 + li, y0 - 1 + lj);
+  R ve[3][UH], vb[3][UH];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R *__restrict__ pe = S.E[cur][c];
+    const R *__restrict__ pb = S.B[cur][c];
+#pragma unroll
+    for (int u = 0; u < UH; ++u) {
+      const int lj = hl[u] >> 8, li = hl[u] & 255;
+      ve[c][u] = in[u] ? pe[off[u]] : R(0);
+      vb[c][u] = in[u] && lj < BH && li < BW ? pb[off[u]] : R(0);
+    }
   }
-  // the current that drives E: this step's deposit, or its filtered copy
-  const bool filtered = S.Jf[0] != nullptr;
-  for (int k = threadIdx.x; k < 3 * JH * JW; k += blockDim.x) {
-    const int c = k / (JH * JW), r = k - c * (JH * JW);
-    const int lj = r / JW, li = r - lj * JW;
-    sj[c][lj][li] = filtered ? fld(S, S.Jf[c], x0 + li, y0 + lj)
-                             : fld_j(S, cur, c, x0 + li, y0 + lj);
+  // J on local [0, X] x [0, Y]: halo cells (li, lj) >= (1, 1)
+  const auto j_cell = [&](int u) {
+    const int lj = hl[u] >> 8, li = hl[u] & 255;
+    return lj >= 1 && li >= 1 && lj <= JH && li <= JW;
+  };
+  if (filtered) {
+    R vj[3][UH];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R *__restrict__ pj = S.Jf[c];
+#pragma unroll
+      for (int u = 0; u < UH; ++u)
+        vj[c][u] = in[u] && j_cell(u) ? pj[off[u]] : R(0);
+    }
+#pragma unroll
+    for (int u = 0; u < UH; ++u) {
+      if (!j_cell(u) || threadIdx.x + u * kThreads >= HN) continue;
+      const int lj = (hl[u] >> 8) - 1, li = (hl[u] & 255) - 1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sj[c][lj][li] = vj[c][u];
+    }
+  } else {
+    // the raw deposit (FP32: int64 fixed point), scaled after the wait
+    JRaw<R> vj[3][UH];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const JRaw<R> *__restrict__ pj = j_plane(S, cur, c);
+#pragma unroll
+      for (int u = 0; u < UH; ++u)
+        vj[c][u] = in[u] && j_cell(u) ? pj[off[u]] : JRaw<R>(0);
+    }
+#pragma unroll
+    for (int u = 0; u < UH; ++u) {
+      if (!j_cell(u) || threadIdx.x + u * kThreads >= HN) continue;
+      const int lj = (hl[u] >> 8) - 1, li = (hl[u] & 255) - 1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sj[c][lj][li] = j_scale(S, c, vj[c][u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < UH; ++u) {
+    if (threadIdx.x + u * kThreads >= HN) continue;
+    const int lj = hl[u] >> 8, li = hl[u] & 255;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      se[c][lj][li] = ve[c][u];
+      if (lj < BH && li < BW) sb[c][lj][li] = vb[c][u];
+    }
   }
   __syncthreads();
+
+  const int shift = s_shift;
 
   // B^{n+1/2} on local [-1, X] x [-1, Y]; sb index = local + 1
   for (int k = threadIdx.x; k < BH * BW; k += blockDim.x) {
@@ -148,7 +276,7 @@ __global__ void __launch_bounds__(kThreads)
   // B^{n+1} on the block's own cells (one per thread) and write back
   const int i = threadIdx.x % X, j = threadIdx.x / X;
   const int gi = x0 + i, gj = y0 + j;
-  double e2 = 0.0, b2 = 0.0;
+  R e2 = R(0), b2 = R(0);
   if (gi < S.nx && gj < S.ny) {
     const R ez = se[2][j + 1][i + 1];
     const R nbx = sb[0][j + 1][i + 1] - h * (se[2][j + 2][i + 1] - ez) * rdy;
@@ -158,8 +286,8 @@ __global__ void __launch_bounds__(kThreads)
                        (se[0][j + 2][i + 1] - se[0][j + 1][i + 1]) * rdy);
     const R ex = se[0][j + 1][i + 1], ey = se[1][j + 1][i + 1];
     if (do_energy) {
-      e2 = (double)(ex * ex + ey * ey + ez * ez);
-      b2 = (double)(nbx * nbx + nby * nby + nbz * nbz);
+      e2 = ex * ex + ey * ey + ez * ez;
+      b2 = nbx * nbx + nby * nby + nbz * nbz;
     }
     const size_t row = (size_t)gj * S.ld;
     const int wi = gi - shift;
@@ -184,13 +312,8 @@ __global__ void __launch_bounds__(kThreads)
         S.J[nxt][c][row + gi] = R(0);
     }
   }
-  if (do_energy) {
-    const size_t b = (size_t)it.y * 2;
-    e2 = block_sum(e2, red);
-    if (threadIdx.x == 0) S.part_fld[b] = e2;
-    b2 = block_sum(b2, red);
-    if (threadIdx.x == 0) S.part_fld[b + 1] = b2;
-  }
+  if (do_energy)
+    block_sum2_store(e2, b2, red, S.part_fld + (size_t)it.y * 2);
 }
 
 // Compensated binomial filter of the current (optional; Sec. 2.2 digital

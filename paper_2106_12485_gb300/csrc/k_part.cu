@@ -16,9 +16,11 @@ namespace zp {
 // the entries whose cell lies in this tile and appends them behind the tile's
 // stayers.  The neighbours' outboxes are read as one concatenated list in
 // passes of kMigE entries per thread: all entries of a pass are loaded
-// first, a block-wide prefix sum of the kept entries gives their slots, then
-// they are copied, so a tile waits for a few memory round trips instead of
-// one per neighbour, and the order of the arrivals is fixed.  Tiles in the
+// first, a block-wide prefix sum of the kept entries gives their slots and
+// lists them in shared memory in slot order, then each thread copies one
+// listed entry, so a tile waits for a few memory round trips instead of one
+// per neighbour, every lane of a warp copies, and the order of the arrivals
+// is fixed.  Tiles in the
 // last column also receive the new plasma column when the window shifts.
 // Particles that find no room go to the overflow buffer and raise
 // ERR_OVERFLOW.
@@ -58,11 +60,16 @@ __device__ __forceinline__ double window_density(const SpeciesDev<R> &P,
 }
 
 constexpr int kMigE = 8;  // outbox entries per thread and pass
-constexpr int kPT_MIG = kThreads;
+// 128 threads per tile: 8 CTAs per SM at 64 registers, so twice the tiles
+// wait on memory at once than with 256
+constexpr int kPT_MIG = 128;
+constexpr int kWarpsMig = kPT_MIG / 32;
 
-// Exclusive prefix sum of v over the CTA (kThreads threads); total = sum.
+// Exclusive prefix sum of v over the CTA (NT threads); total = sum.
+template <int NT>
 __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum,
                                                     int &total) {
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int x = v;
   for (int o = 1; o < 32; o <<= 1) {
@@ -72,29 +79,34 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum,
   if (lane == 31) wsum[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    int w = lane < kWarps ? wsum[lane] : 0;
+    int w = lane < NW ? wsum[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w += y;
     }
-    if (lane < kWarps) wsum[lane] = w;  // inclusive over warps
+    if (lane < NW) wsum[lane] = w;  // inclusive over warps
   }
   __syncthreads();
   const int before = warp > 0 ? wsum[warp - 1] : 0;
-  total = wsum[kWarps - 1];
+  total = wsum[NW - 1];
   __syncthreads();  // wsum is reused by the next call
   return before + x - v;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPT_MIG)
     migrate_kernel(const SimDev<R> *__restrict__ sims,
                    const int2 *__restrict__ items, BatchStatus *st,
                    OverflowDev<R> ovf) {
   __shared__ int nbl[8];
   __shared__ int nnb;
-  __shared__ int pre[9];  // prefix of the neighbours' outbox counts
-  __shared__ int wsum[kWarps];
+  // per species: the neighbours' outbox counts, then their prefix; the
+  // tile's stayer count, capacity and segment offset
+  __shared__ int pre[kMaxSpecies][9];
+  __shared__ int tcnt[kMaxSpecies], tcap[kMaxSpecies];
+  __shared__ int toff[kMaxSpecies];
+  __shared__ int wsum[kWarpsMig];
+  __shared__ int klist[kPT_MIG * kMigE];  // kept outbox entries of a pass
   __shared__ int cursor;
   const int step = st->step;
   if (frozen(st, step)) return;
@@ -123,6 +135,27 @@ __global__ void __launch_bounds__(kThreads)
       }
     nnb = m;
   }
+  __syncthreads();
+  // every count this tile needs, for all species, in one round trip
+  for (int k = threadIdx.x; k < S.nsp * 9; k += blockDim.x) {
+    const int s = k / 9, q = k - s * 9;
+    const SpeciesDev<R> &P = S.sp[s];
+    if (q < nnb) pre[s][q + 1] = P.ob_cnt[nbl[q]];
+    if (q == 8) {
+      tcnt[s] = P.cnt[tile];
+      tcap[s] = P.cap[tile];
+      toff[s] = P.off[tile];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < S.nsp) {
+    int a = 0;
+    pre[threadIdx.x][0] = 0;
+    for (int q = 0; q < nnb; ++q) {
+      a += pre[threadIdx.x][q + 1];
+      pre[threadIdx.x][q + 1] = a;
+    }
+  }
   const int nsh = S.moving_window ? *S.n_shift : 0;
   const bool shift = shift_due(S, step, nsh);
   const bool inject_col = shift && (x0 + tw == S.nx);
@@ -134,60 +167,72 @@ __global__ void __launch_bounds__(kThreads)
     const SpeciesDev<R> &P = S.sp[s];
     const Planes<R> &O = P.buf[nxt];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      pre[0] = 0;
-      for (int q = 0; q < nnb; ++q) pre[q + 1] = pre[q] + P.ob_cnt[nbl[q]];
-    }
-    __syncthreads();
-    const int n_stay = P.cnt[tile];
-    const int cap = P.cap[tile];
-    const size_t base = (size_t)P.off[tile];
-    const int m_all = pre[nnb];
+    const int *pq = pre[s];
+    const int n_stay = tcnt[s];
+    const int cap = tcap[s];
+    const size_t base = (size_t)toff[s];
+    const int m_all = pq[nnb];
     int placed = 0;  // arrivals placed by earlier passes (CTA-uniform)
+    // the outbox planes, read once: the copies below store to global memory,
+    // which would otherwise make the compiler reload every pointer
+    const int ob_cap = P.ob_cap;
+    const int *__restrict__ ob_ix = P.ob_ix;
+    const int *__restrict__ ob_iy = P.ob_iy;
     for (int k0 = 0; k0 < m_all; k0 += kPT_MIG * kMigE) {
-      // pass: load the destination cells of up to kMigE entries per thread
-      int ent[kMigE];
+      // pass: load the destination cells of up to kMigE entries per thread;
+      // entry k of the concatenated list is entry k - pq[q] of neighbour q
+      const auto entry = [&](int k) {
+        int q = 0;
+        while (q + 1 < nnb && pq[q + 1] <= k) ++q;
+        return nbl[q] * ob_cap + (k - pq[q]);
+      };
       unsigned keep = 0;
+      int ent[kMigE];
 #pragma unroll
       for (int j = 0; j < kMigE; ++j) {
         const int k = k0 + j * kPT_MIG + threadIdx.x;
-        ent[j] = -1;
+        ent[j] = 0;
         if (k < m_all) {
-          int q = 0;
-          while (q + 1 < nnb && pre[q + 1] <= k) ++q;
-          const int e = nbl[q] * P.ob_cap + (k - pre[q]);
+          const int e = entry(k);
           ent[j] = e;
-          const int ix = P.ob_ix[e], iy = P.ob_iy[e];
-          if ((iy / S.ty) * S.ntx + ix / S.tx == tile) keep |= 1u << j;
+          const int ix = ob_ix[e], iy = ob_iy[e];
+          if (ix >= x0 && ix < x0 + tw && iy >= y0 && iy < y0 + th)
+            keep |= 1u << j;
         }
       }
       int total;
-      const int first = block_exclusive_scan(__popc(keep), wsum, total);
-      int r = 0;
+      const int first =
+          block_exclusive_scan<kPT_MIG>(__popc(keep), wsum, total);
+      // the kept entries in slot order, then one copy per thread
+      int r = first;
 #pragma unroll
-      for (int j = 0; j < kMigE; ++j) {
-        if (!(keep & (1u << j))) continue;
-        const int e = ent[j];
-        const int ix = P.ob_ix[e], iy = P.ob_iy[e];
+      for (int j = 0; j < kMigE; ++j)
+        if (keep & (1u << j)) klist[r++] = ent[j];
+      __syncthreads();
+      for (int q = threadIdx.x; q < total; q += kPT_MIG) {
+        const int e = klist[q];
+        const int ix = ob_ix[e], iy = ob_iy[e];
+        const R x = P.ob_x[e], y = P.ob_y[e];
+        const R ux = P.ob_ux[e], uy = P.ob_uy[e], uz = P.ob_uz[e];
         const R w = O.w ? P.ob_w[e] : R(1);
         const int id = O.id ? P.ob_id[e] : 0;
-        const int d = n_stay + placed + first + r++;
+        const int d = n_stay + placed + q;
         if (d < cap) {
           const size_t t = base + d;
           O.cell[t] = local_cell(ix - x0, iy - y0);
-          O.x[t] = P.ob_x[e];
-          O.y[t] = P.ob_y[e];
-          O.ux[t] = P.ob_ux[e];
-          O.uy[t] = P.ob_uy[e];
-          O.uz[t] = P.ob_uz[e];
+          O.x[t] = x;
+          O.y[t] = y;
+          O.ux[t] = ux;
+          O.uy[t] = uy;
+          O.uz[t] = uz;
           if (O.w) O.w[t] = w;
           if (O.id) O.id[t] = id;
         } else {
-          park(ovf, st, step, it.x, s, ix, iy, id, P.ob_x[e], P.ob_y[e],
-               P.ob_ux[e], P.ob_uy[e], P.ob_uz[e], w);
+          park(ovf, st, step, it.x, s, ix, iy, id, x, y, ux, uy, uz, w);
         }
       }
       placed += total;
+      __syncthreads();  // klist is refilled by the next pass
     }
     if (threadIdx.x == 0) cursor = placed;
     __syncthreads();
@@ -241,7 +286,7 @@ cudaError_t launch_migrate(const SimDev<R> *sims, const int2 *items,
                            int n_items, BatchStatus *st,
                            const OverflowDev<R> &ovf, cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
-  migrate_kernel<R><<<n_items, kThreads, 0, stream>>>(sims, items, st, ovf);
+  migrate_kernel<R><<<n_items, kPT_MIG, 0, stream>>>(sims, items, st, ovf);
   return cudaGetLastError();
 }
 

@@ -428,9 +428,9 @@ class Batch : public BatchBase {
     return ZPIC_OK;
   }
 
-  // FP32 current: int64 fixed-point sums, scaled as the kernels do (a
-  // double product rounded to float)
-  int get_current_fixed(SimHost<R> &S, const long long *src, double scale,
+  // FP32 current: int64 fixed-point sums, scaled as the kernels do
+  // (fixed_to_float, times the float scale)
+  int get_current_fixed(SimHost<R> &S, const long long *src, float scale,
                         void *dst, int want_f64) {
     const size_t n = (size_t)S.nx * S.ny;
     std::vector<long long> q(n);
@@ -439,7 +439,7 @@ class Batch : public BatchBase {
                             S.ny, cudaMemcpyDeviceToHost, stream_));
     ZP_CU(cudaStreamSynchronize(stream_));
     for (size_t k = 0; k < n; ++k) {
-      const float v = (float)((double)q[k] * scale);
+      const float v = fixed_to_float(q[k]) * scale;
       if (want_f64)
         ((double *)dst)[k] = v;
       else
@@ -996,9 +996,9 @@ class Batch : public BatchBase {
       }
     }
     const double u30 = std::ldexp(1.0, -30);
-    S.dev.jscale[0] = fp32 ? uq * cx * u30 : 1.0;
-    S.dev.jscale[1] = fp32 ? uq * cy * u30 : 1.0;
-    S.dev.jscale[2] = fp32 ? uq * u30 : 1.0;
+    S.dev.jscale[0] = fp32 ? (float)(uq * cx * u30) : 1.0f;
+    S.dev.jscale[1] = fp32 ? (float)(uq * cy * u30) : 1.0f;
+    S.dev.jscale[2] = fp32 ? (float)(uq * u30) : 1.0f;
   }
 
   // Allocates the tile store of species s for per-tile counts cnt.

@@ -19,7 +19,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/zpic.h"
 
@@ -106,9 +108,9 @@ struct SimDev {
   R *Jf[3];                    // filtered current (null: no filter)
   // FP32 tiles accumulate J exactly in two-word fixed point with 2^-30 units
   // of Uq dx/dt, Uq dy/dt, Uq (Uq = max |q0| x max weight, so one segment
-  // contributes at most one unit) and add it to Jq; jscale converts a sum
-  // to J.
-  double jscale[3];
+  // contributes at most one unit) and add it to Jq; a sum v reads as
+  // J = float(v) * jscale, two FP32 roundings (no FP64 on the field path).
+  float jscale[3];
   double *part_kin;            // [kMaxSpecies][ntiles] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
   zpic_energy_rec *hist;       // energy history
@@ -149,12 +151,40 @@ __device__ __forceinline__ bool shift_due(const SimDev<R> &S, int step,
          ((double)(step + 1) * S.dt_d >= (double)(n_shift + 1) * S.dx_d);
 }
 
+// Float with the bit pattern b (host and device).
+__host__ __device__ __forceinline__ float float_of_bits(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
+
+// FP32 value of an int64 fixed-point sum v, |v| < 2^54, in FP32 arithmetic
+// only (a 64-bit integer conversion would run on the FP64 pipe): v = h 2^32
+// + m 2^16 + l with h signed (|h| < 2^22) and m, l in [0, 2^16); each part
+// is exact as a float by the add-the-exponent trick (bits of 2^23 (+2^22)
+// plus the integer, minus that float), then fmaf(h, 2^32, m 2^16) + l rounds
+// twice.  Host and device evaluate the same operations, so the current the
+// field solver uses and the one the API reports agree bit for bit.
+__host__ __device__ __forceinline__ float fixed_to_float(long long v) {
+  const int h = (int)(v >> 32);
+  const uint32_t lo = (uint32_t)(unsigned long long)v;
+  const float fh = float_of_bits(0x4B400000u + (uint32_t)h) - 12582912.0f;
+  const float fm = float_of_bits(0x4B000000u | (lo >> 16)) - 8388608.0f;
+  const float fl = float_of_bits(0x4B000000u | (lo & 0xFFFFu)) - 8388608.0f;
+  const float hm = fmaf(fh, 4294967296.0f, fm * 65536.0f);
+  return hm + fl;
+}
+
 // This step's deposited current of component c at array index idx, as R.
 template <typename R>
 __device__ __forceinline__ R j_value(const SimDev<R> &S, int cur, int c,
                                      size_t idx) {
   if constexpr (sizeof(R) == 4)
-    return (R)((double)S.Jq[cur][c][idx] * S.jscale[c]);
+    return fixed_to_float(S.Jq[cur][c][idx]) * S.jscale[c];
   else
     return S.J[cur][c][idx];
 }
