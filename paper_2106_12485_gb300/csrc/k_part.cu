@@ -374,24 +374,41 @@ cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
 
 // ---- binning ---------------------------------------------------------------
 
+// Both binning kernels walk the particles warp by warp (lane l takes
+// particle base + l) and add to a tile's counter once per warp and tile: the
+// lanes holding the same tile find each other with __match_any_sync, the
+// first of them adds their number, and each takes its rank among them.  A
+// tile-ordered input (what get_particles returns) thus costs one atomic per
+// warp instead of 32 on the same address.
+__device__ __forceinline__ unsigned lanes_before() {
+  return (1u << (threadIdx.x & 31)) - 1u;
+}
+
 template <typename R>
 __global__ void bin_count_kernel(Staging<R> in, long long n, int nx, int ny,
                                  int tx, int ty, int ntx, int *counts,
                                  int *bad) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int ix = in.ix[p], iy = in.iy[p];
-    const R x = in.x[p], y = in.y[p];
-    const bool ok = ix >= 0 && ix < nx && iy >= 0 && iy < ny && x >= R(0) &&
-                    x < R(1) && y >= R(0) && y < R(1);
-    if (!ok) {
-      atomicAdd(bad, 1);
-      in.tile[p] = -1;
-      continue;
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane);
+       base < n; base += stride) {
+    const long long p = base + lane;
+    int t = -1;
+    if (p < n) {
+      const int ix = in.ix[p], iy = in.iy[p];
+      const R x = in.x[p], y = in.y[p];
+      const bool ok = ix >= 0 && ix < nx && iy >= 0 && iy < ny &&
+                      x >= R(0) && x < R(1) && y >= R(0) && y < R(1);
+      if (ok) {
+        t = (iy / ty) * ntx + ix / tx;
+      } else {
+        atomicAdd(bad, 1);
+      }
+      in.tile[p] = t;
     }
-    const int t = (iy / ty) * ntx + ix / tx;
-    in.tile[p] = t;
-    atomicAdd(&counts[t], 1);
+    // lanes without a tile get keys of their own
+    const unsigned peers = __match_any_sync(0xffffffffu, t >= 0 ? t : -1 - lane);
+    if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&counts[t], __popc(peers));
   }
 }
 
@@ -413,20 +430,41 @@ __global__ void bin_scatter_kernel(Staging<R> in, long long n, SpeciesDev<R> P,
                                    int b, int tx, int ty, int has_w,
                                    int has_id) {
   const Planes<R> &O = P.buf[b];
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int t = in.tile[p];
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane);
+       base < n; base += stride) {
+    const long long p = base + lane;
+    const int t = p < n ? in.tile[p] : -1;
+    // the record, loaded before the slot is known
+    int ix = 0, iy = 0, id = 0;
+    R x = R(0), y = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(1);
+    if (t >= 0) {
+      ix = in.ix[p];
+      iy = in.iy[p];
+      x = in.x[p];
+      y = in.y[p];
+      ux = in.ux[p];
+      uy = in.uy[p];
+      uz = in.uz[p];
+      if (has_w) w = in.w[p];
+      id = has_id ? in.id[p] : (int)p;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, t >= 0 ? t : -1 - lane);
     if (t < 0) continue;
-    const int slot = atomicAdd(&P.cnt[t], 1);
+    const int leader = __ffs(peers) - 1;
+    int slot = 0;
+    if (lane == leader) slot = atomicAdd(&P.cnt[t], __popc(peers));
+    slot = __shfl_sync(peers, slot, leader) + __popc(peers & lanes_before());
     const size_t d = (size_t)P.off[t] + slot;
-    O.cell[d] = local_cell(in.ix[p] % tx, in.iy[p] % ty);
-    O.x[d] = in.x[p];
-    O.y[d] = in.y[p];
-    O.ux[d] = in.ux[p];
-    O.uy[d] = in.uy[p];
-    O.uz[d] = in.uz[p];
-    if (O.w) O.w[d] = has_w ? in.w[p] : R(1);
-    if (O.id) O.id[d] = has_id ? in.id[p] : (int)p;
+    O.cell[d] = local_cell(ix % tx, iy % ty);
+    O.x[d] = x;
+    O.y[d] = y;
+    O.ux[d] = ux;
+    O.uy[d] = uy;
+    O.uz[d] = uz;
+    if (O.w) O.w[d] = w;
+    if (O.id) O.id[d] = id;
   }
 }
 
