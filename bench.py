@@ -312,6 +312,73 @@ def base_line(metric_value, ms, args, dtype, config, **extra):
     return out
 
 
+def batch_workload(args, rank, world):
+    """The batched sweep (256 independent simulations).  With N ranks the
+    simulations are split by longest-processing-time-first on their
+    algorithmic bytes per step (every rank computes the same partition, so
+    nothing is exchanged on the data path); each rank advances its share as
+    one batch (one persistent launch per kernel and step, captured in a CUDA
+    graph), then as per-simulation launches for comparison.  The line gives
+    the whole job: particles of all ranks x steps / the slowest rank's
+    time."""
+    import torch
+    from paper_2106_12485_gb300 import workloads as W
+    from paper_2106_12485_gb300 import zpic as Z
+    from synthetic import plasma as P
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.Stream()
+    specs = P.batch_specs(256)
+    parts = W.lpt_partition(W.batch_costs(specs), world)
+    mine = set(parts[rank])
+    cfgs = [c for i, c in enumerate(W.batch_sweep(specs)) if i in mine]
+    batch = Z.Batch(cfgs)
+    batch.set_stream(stream.cuda_stream)
+    batch.step(args.warmup)
+    batch.sync()
+    n = 0
+    for i in range(len(cfgs)):
+        inf = batch.sim(i).info()
+        n += sum(inf.n_particles[:inf.n_species])
+    barrier(world)
+    ms_b = timed_steps(batch, stream, args.steps, torch)
+    del batch
+    sims = [Z.Sim(c) for c in cfgs]
+    for sm in sims:
+        sm.set_stream(stream.cuda_stream)
+        sm.step(args.warmup)
+    for sm in sims:
+        sm.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for sm in sims:
+            sm.step(1)
+    for sm in sims:
+        sm.sync()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    value, ms_b_max, total = aggregate(float(n) * args.steps, ms_b, world)
+    value_s, ms_s_max, _ = aggregate(float(n) * args.steps, ms_s, world)
+    if rank == 0:
+        print(json.dumps(base_line(
+            value, ms_b_max, args, "f32",
+            {"workload": "batched sweep: 256 independent sims 32-256 cells "
+                         "per side, 4-64 ppc, half thermal, half clouds",
+             "sims": len(specs), "particles": int(all_sum(float(n), world)),
+             "sharding": "LPT over %d ranks on bytes per step" % world},
+            n_gpus=world, scaling="strong",
+            per_sim_launches={"value": value_s,
+                              "ms_per_step": ms_s_max / args.steps},
+            batched_over_per_sim=ms_s_max / ms_b_max)))
+    else:
+        all_sum(float(n), world)
+
+
 def other_workload(args):
     """Lines for the workloads other than the large uniform plasma."""
     import torch
@@ -377,47 +444,6 @@ def other_workload(args):
         print(json.dumps({"workload": "tile-size sweep (autotuner)",
                           "steps": args.steps, "classes": out}))
         return
-    if args.workload == "batch":
-        specs = P.batch_specs(256)
-        cfgs = W.batch_sweep(specs)
-        batch = Z.Batch(cfgs)
-        batch.set_stream(stream.cuda_stream)
-        batch.step(args.warmup)
-        batch.sync()
-        n = 0
-        for i in range(len(cfgs)):
-            inf = batch.sim(i).info()
-            n += sum(inf.n_particles[:inf.n_species])
-        ms_b = timed_steps(batch, stream, args.steps, torch)
-        del batch
-        sims = [Z.Sim(c) for c in cfgs]
-        for sm in sims:
-            sm.set_stream(stream.cuda_stream)
-            sm.step(args.warmup)
-        for sm in sims:
-            sm.sync()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            for sm in sims:
-                sm.step(1)
-        for sm in sims:
-            sm.sync()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_s = e0.elapsed_time(e1)
-        ps = float(n) * args.steps
-        print(json.dumps(base_line(
-            ps / (ms_b / 1e3), ms_b, args, "f32",
-            {"workload": "batched sweep: 256 independent sims 32-256 cells "
-                         "per side, 4-64 ppc, half thermal, half clouds",
-             "sims": len(cfgs), "particles": int(n)},
-            per_sim_launches={"value": ps / (ms_s / 1e3),
-                              "ms_per_step": ms_s / args.steps},
-            batched_over_per_sim=ms_s / ms_b)))
-        return
     if args.workload == "precision":
         # FP32 vs FP64 at equal energy-conservation error: for each form the
         # largest dt of the sweep whose total-energy drift over 100 steps
@@ -471,6 +497,9 @@ def main():
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "batch":
+        batch_workload(args, rank, world)
         return
     if args.workload != "uniform":
         if rank == 0:

@@ -86,6 +86,55 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return v;  // valid in warp 0 lane 0 (and every warp's lane 0)
 }
 
+// Compensated FP64 sum (Kahan-Babuska / Neumaier, with Knuth's branch-free
+// TwoSum): s holds the rounded running sum and c the accumulated rounding
+// errors, so s + c carries the exact sum's leading digits until c itself
+// rounds; the result's error stays near one rounding of the total instead of
+// growing with the number of terms.  Used for the energy diagnostics.
+struct CSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double t = s + x, bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ void add(const CSum &o) {
+    add(o.s);
+    c += o.c;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+// CSum over the CTA in a fixed order (shuffle tree, then warp 0 over the
+// warp sums); the total is valid in thread 0.
+__device__ __forceinline__ double block_csum(CSum v, double *red2) {
+  for (int o = 16; o > 0; o >>= 1) {
+    CSum u;
+    u.s = __shfl_down_sync(0xffffffffu, v.s, o);
+    u.c = __shfl_down_sync(0xffffffffu, v.c, o);
+    v.add(u);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red2[2 * warp] = v.s;
+    red2[2 * warp + 1] = v.c;
+  }
+  __syncthreads();
+  CSum w;
+  if (lane < (int)(blockDim.x >> 5)) {
+    w.s = red2[2 * lane];
+    w.c = red2[2 * lane + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    CSum u;
+    u.s = __shfl_down_sync(0xffffffffu, w.s, o);
+    u.c = __shfl_down_sync(0xffffffffu, w.c, o);
+    w.add(u);
+  }
+  return w.value();
+}
+
 // Sums (e, b) over the CTA and stores the two totals at dst[0], dst[1]:
 // each warp adds its 32 values in R (the cells' squares are R already),
 // thread 0 adds the warp sums in double, in warp order.  Keeps the FP64 work
@@ -401,7 +450,7 @@ cudaError_t launch_yee(const SimDev<R> *sims, const int2 *items, int n_items,
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     end_step_kernel(const SimDev<R> *__restrict__ sims, BatchStatus *st) {
-  __shared__ double red[kWarps];
+  __shared__ double red[2 * kWarps];
   const int step = st->step;
   if (frozen(st, step)) return;
   const SimDev<R> &S = sims[blockIdx.x];
@@ -410,38 +459,43 @@ __global__ void __launch_bounds__(kThreads)
   if (do_energy) {
     const int ntiles = S.ntx * S.nty;
     double kin[kMaxSpecies];
-    // four independent partial sums per thread keep four loads in flight;
-    // they are combined in a fixed order, so the total is reproducible
+    // compensated FP64 sums of the per-tile and per-block partials; four
+    // independent sums per thread keep four loads in flight and are
+    // combined in a fixed order, so the total is reproducible
     const int T4 = 4 * blockDim.x;
     for (int s = 0; s < S.nsp; ++s) {
       const double *pk = S.part_kin + (size_t)s * ntiles;
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      CSum v0, v1, v2, v3;
       int t = threadIdx.x;
       for (; t + 3 * (int)blockDim.x < ntiles; t += T4) {
-        v0 += pk[t];
-        v1 += pk[t + blockDim.x];
-        v2 += pk[t + 2 * blockDim.x];
-        v3 += pk[t + 3 * blockDim.x];
+        v0.add(pk[t]);
+        v1.add(pk[t + blockDim.x]);
+        v2.add(pk[t + 2 * blockDim.x]);
+        v3.add(pk[t + 3 * blockDim.x]);
       }
-      for (; t < ntiles; t += blockDim.x) v0 += pk[t];
-      kin[s] = block_sum((v0 + v1) + (v2 + v3), red) * S.sp[s].kin_scale;
+      for (; t < ntiles; t += blockDim.x) v0.add(pk[t]);
+      v0.add(v1);
+      v2.add(v3);
+      v0.add(v2);
+      kin[s] = block_csum(v0, red) * S.sp[s].kin_scale;
     }
     const int nyb = S.ybx * S.yby;
-    double e0 = 0.0, e1 = 0.0, b0 = 0.0, b1 = 0.0;
+    CSum e0, e1, b0, b1;
     int t = threadIdx.x;
     for (; t + (int)blockDim.x < nyb; t += 2 * blockDim.x) {
-      e0 += S.part_fld[2 * (size_t)t];
-      b0 += S.part_fld[2 * (size_t)t + 1];
-      e1 += S.part_fld[2 * (size_t)(t + blockDim.x)];
-      b1 += S.part_fld[2 * (size_t)(t + blockDim.x) + 1];
+      e0.add(S.part_fld[2 * (size_t)t]);
+      b0.add(S.part_fld[2 * (size_t)t + 1]);
+      e1.add(S.part_fld[2 * (size_t)(t + blockDim.x)]);
+      b1.add(S.part_fld[2 * (size_t)(t + blockDim.x) + 1]);
     }
     for (; t < nyb; t += blockDim.x) {
-      e0 += S.part_fld[2 * (size_t)t];
-      b0 += S.part_fld[2 * (size_t)t + 1];
+      e0.add(S.part_fld[2 * (size_t)t]);
+      b0.add(S.part_fld[2 * (size_t)t + 1]);
     }
-    double e = e0 + e1, b = b0 + b1;
-    e = block_sum(e, red);
-    b = block_sum(b, red);
+    e0.add(e1);
+    b0.add(b1);
+    const double e = block_csum(e0, red);
+    const double b = block_csum(b0, red);
     if (threadIdx.x == 0) {
       const int rec = (step + 1) / S.energy_every - 1 - S.hist_skip;
       const double area = S.dx_d * S.dy_d;
@@ -496,31 +550,31 @@ cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     field_energy_rows_kernel(FieldPtrs<R> f, int nx, int ld, double *scratch) {
-  __shared__ double red[kWarps];
+  __shared__ double red[2 * kWarps];
   const size_t row = (size_t)blockIdx.x * ld;
-  double e = 0.0, b = 0.0;
+  CSum e, b;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const R ex = f.e[0][row + i], ey = f.e[1][row + i], ez = f.e[2][row + i];
     const R bx = f.b[0][row + i], by = f.b[1][row + i], bz = f.b[2][row + i];
-    e += (double)(ex * ex + ey * ey + ez * ez);
-    b += (double)(bx * bx + by * by + bz * bz);
+    e.add((double)ex * ex + (double)ey * ey + (double)ez * ez);
+    b.add((double)bx * bx + (double)by * by + (double)bz * bz);
   }
-  e = block_sum(e, red);
-  if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x] = e;
-  b = block_sum(b, red);
-  if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x + 1] = b;
+  const double es = block_csum(e, red);
+  if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x] = es;
+  const double bs = block_csum(b, red);
+  if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x + 1] = bs;
 }
 
 __global__ void __launch_bounds__(kThreads)
     field_energy_final_kernel(double *scratch, int ny, double half_area) {
-  __shared__ double red[kWarps];
-  double e = 0.0, b = 0.0;
+  __shared__ double red[2 * kWarps];
+  CSum es, bs;
   for (int j = threadIdx.x; j < ny; j += blockDim.x) {
-    e += scratch[2 * (size_t)j];
-    b += scratch[2 * (size_t)j + 1];
+    es.add(scratch[2 * (size_t)j]);
+    bs.add(scratch[2 * (size_t)j + 1]);
   }
-  e = block_sum(e, red);
-  b = block_sum(b, red);
+  const double e = block_csum(es, red);
+  const double b = block_csum(bs, red);
   if (threadIdx.x == 0) {
     scratch[2 * (size_t)ny] = half_area * e;
     scratch[2 * (size_t)ny + 1] = half_area * b;

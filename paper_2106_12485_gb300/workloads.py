@@ -105,3 +105,45 @@ def batch_sweep(specs, dt=0.07, d=0.1, precision=Z.FP32, **kw):
                        sim_index=i, **kw)
         cfgs.append(c)
     return cfgs
+
+
+# ---- sharding independent simulations over GPUs ---------------------------
+
+def batch_particles(spec):
+    """Particles of one batched simulation at creation: the whole box for
+    thermal plasma; for the cloud collision two clouds (columns
+    [nx/8, 3nx/8) and [5nx/8, 7nx/8)), each with electrons and positrons."""
+    k2 = spec["ppc_side"] ** 2
+    if spec["kind"] == "thermal":
+        return spec["nx"] * spec["ny"] * k2
+    nx = spec["nx"]
+    width = (3 * nx // 8 - nx // 8) + (7 * nx // 8 - 5 * nx // 8)
+    return 2 * width * spec["ny"] * k2
+
+
+def batch_costs(specs, bytes_per_particle=44, bytes_per_cell=36):
+    """Cost of one step of each simulation in algorithmic HBM bytes: the
+    particle record read and written once (44 B in FP32) plus E, B read and
+    J written once per cell (36 B)."""
+    return [bytes_per_particle * batch_particles(s) +
+            bytes_per_cell * s["nx"] * s["ny"] for s in specs]
+
+
+def lpt_partition(costs, n_parts):
+    """Longest-processing-time-first assignment of independent jobs to
+    n_parts workers: jobs in decreasing cost (ties by index) each go to the
+    worker with the least load so far (ties to the lowest worker).  The
+    result is deterministic, so every rank computes the same partition
+    without exchanging anything; the largest load exceeds the smallest by
+    at most the largest job.  Returns one ascending list of job indices per
+    worker."""
+    if n_parts < 1:
+        raise ValueError("n_parts must be >= 1")
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0] * n_parts
+    parts = [[] for _ in range(n_parts)]
+    for i in order:
+        w = min(range(n_parts), key=lambda p: (load[p], p))
+        parts[w].append(i)
+        load[w] += costs[i]
+    return [sorted(p) for p in parts]
