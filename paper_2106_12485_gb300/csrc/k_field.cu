@@ -106,8 +106,8 @@ struct CSum {
 };
 
 // CSum over the CTA in a fixed order (shuffle tree, then warp 0 over the
-// warp sums); the total is valid in thread 0.
-__device__ __forceinline__ double block_csum(CSum v, double *red2) {
+// warp sums); the result is valid in thread 0.
+__device__ __forceinline__ CSum block_csum(CSum v, double *red2) {
   for (int o = 16; o > 0; o >>= 1) {
     CSum u;
     u.s = __shfl_down_sync(0xffffffffu, v.s, o);
@@ -132,7 +132,7 @@ __device__ __forceinline__ double block_csum(CSum v, double *red2) {
     u.c = __shfl_down_sync(0xffffffffu, w.c, o);
     w.add(u);
   }
-  return w.value();
+  return w;
 }
 
 // Sums (e, b) over the CTA and stores the two totals at dst[0], dst[1]:
@@ -447,67 +447,148 @@ cudaError_t launch_yee(const SimDev<R> *sims, const int2 *items, int n_items,
 
 // ---- end of step ----------------------------------------------------------
 
+// kEndSlices CTAs per simulation (blockIdx.x = sim * kEndSlices + slice).
+// On an energy step each CTA sums its slice of the per-tile kinetic and
+// per-Yee-block field partials in compensated FP64 and stores (sum, error)
+// per quantity; the last slice of the simulation to finish (ticket)
+// combines the slices in slice order and writes the record.  The slicing
+// depends on the simulation alone, so a simulation gives the same bits in a
+// batch and on its own.  One CTA per simulation (energy steps: that last
+// slice; otherwise slice 0) advances the window counter; every CTA takes the
+// step ticket (after it has read the step), and the last one advances the
+// step.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     end_step_kernel(const SimDev<R> *__restrict__ sims, BatchStatus *st) {
-  __shared__ double red[2 * kWarps];
+  constexpr int G = kEndSlices;
+  __shared__ double red[kWarps * kEndQ * 2];
+  __shared__ double s_part[G * kEndQ * 2];
+  __shared__ double s_q[kEndQ * 2];
+  __shared__ int s_last;
   const int step = st->step;
   if (frozen(st, step)) return;
-  const SimDev<R> &S = sims[blockIdx.x];
+  const int sim = blockIdx.x / G, g = blockIdx.x - sim * G;
+  const SimDev<R> &S = sims[sim];
   const bool do_energy =
       S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
+  bool owner = g == 0;
   if (do_energy) {
     const int ntiles = S.ntx * S.nty;
-    double kin[kMaxSpecies];
-    // compensated FP64 sums of the per-tile and per-block partials; four
-    // independent sums per thread keep four loads in flight and are
-    // combined in a fixed order, so the total is reproducible
-    const int T4 = 4 * blockDim.x;
-    for (int s = 0; s < S.nsp; ++s) {
-      const double *pk = S.part_kin + (size_t)s * ntiles;
-      CSum v0, v1, v2, v3;
-      int t = threadIdx.x;
-      for (; t + 3 * (int)blockDim.x < ntiles; t += T4) {
-        v0.add(pk[t]);
-        v1.add(pk[t + blockDim.x]);
-        v2.add(pk[t + 2 * blockDim.x]);
-        v3.add(pk[t + 3 * blockDim.x]);
-      }
-      for (; t < ntiles; t += blockDim.x) v0.add(pk[t]);
-      v0.add(v1);
-      v2.add(v3);
-      v0.add(v2);
-      kin[s] = block_csum(v0, red) * S.sp[s].kin_scale;
-    }
+    const int nsp = S.nsp;
+    // quantity k: kinetic energy of species k (k < nsp), E^2 (kMaxSpecies),
+    // B^2 (kMaxSpecies + 1); the others stay zero
+    auto used = [&](int k) { return k >= kMaxSpecies || k < nsp; };
+    // this slice: tiles [t0, t1), Yee blocks [y0, y1)
+    const int t0 = (int)((long long)ntiles * g / G);
+    const int t1 = (int)((long long)ntiles * (g + 1) / G);
     const int nyb = S.ybx * S.yby;
-    CSum e0, e1, b0, b1;
-    int t = threadIdx.x;
-    for (; t + (int)blockDim.x < nyb; t += 2 * blockDim.x) {
-      e0.add(S.part_fld[2 * (size_t)t]);
-      b0.add(S.part_fld[2 * (size_t)t + 1]);
-      e1.add(S.part_fld[2 * (size_t)(t + blockDim.x)]);
-      b1.add(S.part_fld[2 * (size_t)(t + blockDim.x) + 1]);
+    const int y0 = (int)((long long)nyb * g / G);
+    const int y1 = (int)((long long)nyb * (g + 1) / G);
+    CSum v[kEndQ];
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      if (s >= nsp) continue;
+      const double *pk = S.part_kin + (size_t)s * ntiles;
+      for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) v[s].add(pk[t]);
     }
-    for (; t < nyb; t += blockDim.x) {
-      e0.add(S.part_fld[2 * (size_t)t]);
-      b0.add(S.part_fld[2 * (size_t)t + 1]);
+    for (int t = y0 + threadIdx.x; t < y1; t += blockDim.x) {
+      v[kMaxSpecies].add(S.part_fld[2 * (size_t)t]);
+      v[kMaxSpecies + 1].add(S.part_fld[2 * (size_t)t + 1]);
     }
-    e0.add(e1);
-    b0.add(b1);
-    const double e = block_csum(e0, red);
-    const double b = block_csum(b0, red);
-    if (threadIdx.x == 0) {
+    // all quantities over the CTA at once, in a fixed order: shuffle tree
+    // in each warp, then warp 0 over the warp sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < kEndQ; ++k) {
+        if (!used(k)) continue;
+        CSum u;
+        u.s = __shfl_down_sync(0xffffffffu, v[k].s, o);
+        u.c = __shfl_down_sync(0xffffffffu, v[k].c, o);
+        v[k].add(u);
+      }
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < kEndQ; ++k) {
+        red[(warp * kEndQ + k) * 2] = v[k].s;
+        red[(warp * kEndQ + k) * 2 + 1] = v[k].c;
+      }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int k = 0; k < kEndQ; ++k) {
+        CSum w;
+        if (lane < kWarps) {
+          w.s = red[(lane * kEndQ + k) * 2];
+          w.c = red[(lane * kEndQ + k) * 2 + 1];
+        }
+        v[k] = w;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < kEndQ; ++k) {
+          if (!used(k)) continue;
+          CSum u;
+          u.s = __shfl_down_sync(0xffffffffu, v[k].s, o);
+          u.c = __shfl_down_sync(0xffffffffu, v[k].c, o);
+          v[k].add(u);
+        }
+      }
+      if (lane == 0) {
+        double *slot = S.epart + (size_t)g * kEndQ * 2;
+#pragma unroll
+        for (int k = 0; k < kEndQ; ++k) {
+          slot[2 * k] = v[k].s;
+          slot[2 * k + 1] = v[k].c;
+        }
+        __threadfence();
+        s_last = atomicAdd(S.eticket, 1) == G - 1;
+      }
+    }
+    __syncthreads();
+    owner = s_last != 0;
+    if (owner) {
+      // every slice's values, read from L2 by all threads at once; thread k
+      // combines quantity k over the slices in slice order
+      __threadfence();
+      for (int k = threadIdx.x; k < G * kEndQ * 2; k += blockDim.x)
+        s_part[k] = __ldcg(S.epart + k);
+      __syncthreads();
+      if (threadIdx.x < kEndQ) {
+        const int k = threadIdx.x;
+        CSum q;
+        if (used(k))
+          for (int h = 0; h < G; ++h) {
+            CSum u;
+            u.s = s_part[(h * kEndQ + k) * 2];
+            u.c = s_part[(h * kEndQ + k) * 2 + 1];
+            q.add(u);
+          }
+        s_q[2 * k] = q.s;
+        s_q[2 * k + 1] = q.c;
+      }
+      __syncthreads();
+    }
+    if (owner && threadIdx.x == 0) {
+      *S.eticket = 0;  // for the next energy step
+      auto total = [&](int k) { return s_q[2 * k] + s_q[2 * k + 1]; };
       const int rec = (step + 1) / S.energy_every - 1 - S.hist_skip;
       const double area = S.dx_d * S.dy_d;
-      bool bad = !isfinite(e) || !isfinite(b);
+      const double ev = total(kMaxSpecies);
+      const double bv = total(kMaxSpecies + 1);
+      bool bad = !isfinite(ev) || !isfinite(bv);
+      double kin[kMaxSpecies];
+      for (int s = 0; s < kMaxSpecies; ++s)
+        kin[s] = s < S.nsp ? total(s) * S.sp[s].kin_scale : 0.0;
       if (rec >= 0 && rec < S.hist_cap) {
         zpic_energy_rec &r = S.hist[rec];
         r.step = step + 1;
         r.n_species = S.nsp;
-        r.wE = 0.5 * e * area;
-        r.wB = 0.5 * b * area;
+        r.wE = 0.5 * ev * area;
+        r.wB = 0.5 * bv * area;
         for (int s = 0; s < kMaxSpecies; ++s) {
-          r.kin[s] = s < S.nsp ? kin[s] : 0.0;
+          r.kin[s] = kin[s];
           if (s < S.nsp && !isfinite(kin[s])) bad = true;
         }
         *S.hist_n = rec + 1;
@@ -519,7 +600,8 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   if (threadIdx.x == 0) {
-    if (S.moving_window && shift_due(S, step, *S.n_shift)) *S.n_shift += 1;
+    if (owner && S.moving_window && shift_due(S, step, *S.n_shift))
+      *S.n_shift += 1;
     __threadfence();
     const int t = atomicAdd(&st->blocks_done, 1);
     if (t == (int)gridDim.x - 1) {
@@ -534,7 +616,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename R>
 cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
                             BatchStatus *st, cudaStream_t stream) {
-  end_step_kernel<R><<<n_sims, kThreads, 0, stream>>>(sims, st);
+  end_step_kernel<R><<<n_sims * kEndSlices, kThreads, 0, stream>>>(sims, st);
   return cudaGetLastError();
 }
 
@@ -559,9 +641,9 @@ __global__ void __launch_bounds__(kThreads)
     e.add((double)ex * ex + (double)ey * ey + (double)ez * ez);
     b.add((double)bx * bx + (double)by * by + (double)bz * bz);
   }
-  const double es = block_csum(e, red);
+  const double es = block_csum(e, red).value();
   if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x] = es;
-  const double bs = block_csum(b, red);
+  const double bs = block_csum(b, red).value();
   if (threadIdx.x == 0) scratch[2 * (size_t)blockIdx.x + 1] = bs;
 }
 
@@ -573,8 +655,8 @@ __global__ void __launch_bounds__(kThreads)
     es.add(scratch[2 * (size_t)j]);
     bs.add(scratch[2 * (size_t)j + 1]);
   }
-  const double e = block_csum(es, red);
-  const double b = block_csum(bs, red);
+  const double e = block_csum(es, red).value();
+  const double b = block_csum(bs, red).value();
   if (threadIdx.x == 0) {
     scratch[2 * (size_t)ny] = half_area * e;
     scratch[2 * (size_t)ny + 1] = half_area * b;

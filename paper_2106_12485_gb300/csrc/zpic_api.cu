@@ -271,7 +271,7 @@ struct SimHost {
   int nx, ny, ld, tx, ty, ntx, nty, ntiles, ybx, yby;
   double dx, dy, dt;
   DevMem fields;           // 18 planes of ny * ld
-  DevMem part_kin, part_fld, hist, small, energy_rows;
+  DevMem part_kin, part_fld, epart, hist, small, energy_rows;
   int hist_cap = 0;
   std::vector<SpeciesHost<R>> sp;
   SimDev<R> dev{};         // host copy of the descriptor
@@ -893,12 +893,15 @@ class Batch : public BatchBase {
     for (int c3 = 0; c3 < 3; ++c3)
       D.Jf[c3] = filter ? jf + (size_t)c3 * plane : nullptr;
     if (!dalloc(S.part_kin, sizeof(double) * S.ntiles * kMaxSpecies) ||
-        !dalloc(S.part_fld, sizeof(double) * 2 * S.ybx * S.yby))
+        !dalloc(S.part_fld, sizeof(double) * 2 * S.ybx * S.yby) ||
+        !dalloc(S.epart, sizeof(double) * 2 * kEndSlices * kEndQ))
       return fail(ZPIC_ENOMEM, "partials");
     ZP_CU(cudaMemsetAsync(S.part_kin.p, 0, S.part_kin.bytes, stream_));
     ZP_CU(cudaMemsetAsync(S.part_fld.p, 0, S.part_fld.bytes, stream_));
     D.part_kin = (double *)S.part_kin.p;
     D.part_fld = (double *)S.part_fld.p;
+    ZP_CU(cudaMemsetAsync(S.epart.p, 0, S.epart.bytes, stream_));
+    D.epart = (double *)S.epart.p;
     S.hist_cap = c.energy_every > 0 ? 4096 : 1;
     if (!dalloc(S.hist, sizeof(zpic_energy_rec) * S.hist_cap))
       return fail(ZPIC_ENOMEM, "history");
@@ -908,13 +911,14 @@ class Batch : public BatchBase {
     D.hist_skip = 0;
     if (!dalloc(S.energy_rows, sizeof(double) * (2 * (size_t)S.ny + 2)))
       return fail(ZPIC_ENOMEM, "energy scratch");
-    if (!dalloc(S.small, sizeof(int) * (2 + 2 * kMaxSpecies)))
+    if (!dalloc(S.small, sizeof(int) * (3 + 2 * kMaxSpecies)))
       return fail(ZPIC_ENOMEM, "counters");
     ZP_CU(cudaMemsetAsync(S.small.p, 0, S.small.bytes, stream_));
     D.hist_n = (int *)S.small.p;
     D.n_shift = (int *)S.small.p + 1;
     D.removed = (int *)S.small.p + 2;
     D.ob_need = (int *)S.small.p + 2 + kMaxSpecies;
+    D.eticket = (int *)S.small.p + 2 + 2 * kMaxSpecies;
 
     // species: initial per-tile counts from the profile, then capacities
     S.sp.resize(c.n_species);
@@ -1553,8 +1557,8 @@ class Batch : public BatchBase {
                             &P.ob_iy, &P.ob_id, &P.ob_x, &P.ob_y, &P.ob_ux,
                             &P.ob_uy, &P.ob_uz, &P.ob_w})
             dfree(*m);
-        for (DevMem *m : {&S.fields, &S.part_kin, &S.part_fld, &S.hist, &S.small,
-                          &S.energy_rows})
+        for (DevMem *m : {&S.fields, &S.part_kin, &S.part_fld, &S.epart,
+                          &S.hist, &S.small, &S.energy_rows})
           dfree(*m);
       }
       for (DevMem *m : {&st_mem_, &sims_dev_, &items_, &yee_items_, &ov_sim_,

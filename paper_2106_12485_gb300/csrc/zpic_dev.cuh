@@ -30,6 +30,11 @@ namespace zp {
 constexpr int kMaxSpecies = ZPIC_MAX_SPECIES;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Most CTAs that share the end-of-step energy reduction of one simulation
+// (each sums a slice of the partials; the last one to finish combines them).
+constexpr int kEndSlices = 16;
+// Values of one slice: kinetic energy per species, E^2, B^2.
+constexpr int kEndQ = kMaxSpecies + 2;
 
 // BatchStatus::error bits
 constexpr int ERR_OVERFLOW = 1;  // particles parked in the overflow buffer
@@ -113,6 +118,9 @@ struct SimDev {
   float jscale[3];
   double *part_kin;            // [kMaxSpecies][ntiles] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
+  double *epart;               // [kEndSlices][kEndQ][2] compensated sums
+                               // (sum, error) of the end-of-step slices
+  int *eticket;                // slices of this simulation finished
   zpic_energy_rec *hist;       // energy history
   int hist_cap;
   int hist_skip;               // records before the first one kept (a run
