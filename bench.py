@@ -598,13 +598,24 @@ def main():
     # ---- CPU oracle baseline (rank 0 only) ----------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        # all host threads (the particle-decomposed mode of Sec. 3.1) on a
+        # box of cpu_sample^2 cells, and one thread on a quarter of it
         nthreads = os.cpu_count() or 1
-        v, n, secs = oracle_sample(args.cpu_sample, args.ppc, 2, nthreads)
+        steps_mt = 10
+        v, n, secs = oracle_sample(args.cpu_sample, args.ppc, steps_mt,
+                                   nthreads)
+        c1 = max(args.cpu_sample // 2, 8)
+        v1, n1, secs1 = oracle_sample(c1, args.ppc, 2, 1)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": nthreads,
                "kind": "oracle",
                "sample": "%dx%d periodic box of the same plasma (%d "
-                         "particles), 2 steps, FP64, %d threads, %.1f s" %
-                         (args.cpu_sample, args.cpu_sample, n, nthreads, secs)}
+                         "particles), %d steps, FP64, %d threads, %.1f s" %
+                         (args.cpu_sample, args.cpu_sample, n, steps_mt,
+                          nthreads, secs),
+               "single_thread": {
+                   "value": v1, "unit": "particle-steps/s", "cores": 1,
+                   "sample": "%dx%d box (%d particles), 2 steps, %.1f s" %
+                             (c1, c1, n1, secs1)}}
 
     if rank == 0:
         out = {

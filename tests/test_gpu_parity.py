@@ -278,3 +278,22 @@ def test_current_filter_matches_oracle(precision, tol):
         a, b = raw.field(k), filt.field(k)
         assert np.sum(np.diff(b, axis=1) ** 2) < 0.5 * np.sum(np.diff(a, axis=1) ** 2)
 
+
+
+@pytest.mark.parametrize("precision", [Z.FP32, Z.FP64])
+def test_field_energy_sum_is_compensated(precision):
+    # one cell of E_x = 1e9 (square 1e18, ulp 128) among 262,143 cells of
+    # E_x = 1: a plain FP64 sum drops every +1 added to the huge partial
+    # (255 of them in the first row's first thread alone, two ulps); the
+    # compensated sum returns the exactly rounded total.  dx dy / 2 = 1/8
+    # keeps the final scaling exact.
+    nx, ny = 65536, 4
+    ex = np.ones((ny, nx))
+    ex[0, 0] = 1e9
+    cfg = Z.config(nx, ny, (nx * 0.5, ny * 0.5), 0.3, [], precision=precision)
+    gpu = Z.Sim(cfg)
+    gpu.set_field("ex", ex)
+    wE, wB = gpu.field_energy()
+    exact = 10 ** 18 + (nx * ny - 1)
+    assert wB == 0.0
+    assert wE / 0.125 == float(exact)
