@@ -88,6 +88,16 @@ struct DevMem {
   size_t bytes = 0;
 };
 
+// Waits for a stream when it goes out of scope: a call that queued copies
+// to or from the caller's host memory on a side stream returns only when
+// they are done, on its error paths too.
+struct StreamDrain {
+  cudaStream_t s;
+  ~StreamDrain() {
+    if (s) cudaStreamSynchronize(s);
+  }
+};
+
 class Allocator {
  public:
   explicit Allocator(cudaStream_t s)
@@ -299,6 +309,9 @@ class Batch : public BatchBase {
     }
     ZP_CU(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
     stream_ = own_stream_;
+    ZP_CU(cudaStreamCreateWithFlags(&cpy_, cudaStreamNonBlocking));
+    ZP_CU(cudaEventCreateWithFlags(&ev_pos_, cudaEventDisableTiming));
+    ZP_CU(cudaEventCreateWithFlags(&ev_mom_, cudaEventDisableTiming));
     alloc_.reset(new Allocator(stream_));
     sims_.resize(n);
     for (int i = 0; i < n; ++i) ZP_TRY(init_sim(i, cfgs[i]));
@@ -504,10 +517,47 @@ class Batch : public BatchBase {
     ZP_TRY(ensure_staging(n + 1));
     ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * off.size(),
                           cudaMemcpyHostToDevice, stream_));
+    const bool same = (d->precision == ZPIC_FP64) == (sizeof(R) == 8);
+    if (same) {
+      // compaction in kChunks tile ranges on the library stream; each
+      // range's copies to the host run on the transfer stream while the
+      // next range is compacted
+      StreamDrain drain{cpy_};
+      constexpr int kChunks = 4;
+      const int nt = t1 - t0;
+      void *dsts[9] = {d->ix, d->iy, d->id, d->x, d->y, d->ux, d->uy, d->uz,
+                       d->w};
+      const void *srcs[9] = {stg_.ix, stg_.iy, stg_.id, stg_.x, stg_.y,
+                             stg_.ux, stg_.uy, stg_.uz, stg_.w};
+      const size_t esz[9] = {4, 4, 4, sizeof(R), sizeof(R), sizeof(R),
+                             sizeof(R), sizeof(R), sizeof(R)};
+      for (int c = 0; c < kChunks; ++c) {
+        const int a = t0 + (int)((long long)nt * c / kChunks);
+        const int b = t0 + (int)((long long)nt * (c + 1) / kChunks);
+        if (a == b) continue;
+        ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty,
+                                S.ntx, a, b - a,
+                                (const long long *)stg_off_.p + (a - t0),
+                                stg_, stream_));
+        const long long p0 = off[a - t0], p1 = b < t1 ? off[b - t0] : n;
+        if (p1 == p0) continue;
+        ZP_CU(cudaEventRecord(ev_pos_, stream_));
+        ZP_CU(cudaStreamWaitEvent(cpy_, ev_pos_, 0));
+        for (int k = 0; k < 9; ++k) {
+          if (!dsts[k]) continue;
+          ZP_CU(cudaMemcpyAsync((char *)dsts[k] + esz[k] * p0,
+                                (const char *)srcs[k] + esz[k] * p0,
+                                esz[k] * (p1 - p0), cudaMemcpyDeviceToHost,
+                                cpy_));
+        }
+      }
+      ZP_CU(cudaStreamSynchronize(cpy_));
+      ZP_CU(cudaStreamSynchronize(stream_));
+      return ZPIC_OK;
+    }
     ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty, S.ntx,
                             t0, t1 - t0, (const long long *)stg_off_.p, stg_,
                             stream_));
-    const bool same = (d->precision == ZPIC_FP64) == (sizeof(R) == 8);
     ZP_CU(cudaMemcpyAsync(d->ix, stg_.ix, 4 * n, cudaMemcpyDeviceToHost, stream_));
     ZP_CU(cudaMemcpyAsync(d->iy, stg_.iy, 4 * n, cudaMemcpyDeviceToHost, stream_));
     if (d->id)
@@ -548,28 +598,44 @@ class Batch : public BatchBase {
     const long long n = (long long)src->n;
     ZP_TRY(ensure_staging(n + 1));
     const bool same = (src->precision == ZPIC_FP64) == (sizeof(R) == 8);
+    StreamDrain drain{cpy_};
     ZP_CU(cudaMemcpyAsync(stg_.ix, src->ix, 4 * n, cudaMemcpyHostToDevice, stream_));
     ZP_CU(cudaMemcpyAsync(stg_.iy, src->iy, 4 * n, cudaMemcpyHostToDevice, stream_));
-    if (src->id)
-      ZP_CU(cudaMemcpyAsync(stg_.id, src->id, 4 * n, cudaMemcpyHostToDevice, stream_));
     const void *srcs[6] = {src->x, src->y, src->ux, src->uy, src->uz, src->w};
     R *dsts[6] = {stg_.x, stg_.y, stg_.ux, stg_.uy, stg_.uz, stg_.w};
-    std::vector<R> tmp;
-    for (int a = 0; a < 6; ++a) {
-      if (!srcs[a]) continue;
-      if (same) {
+    cudaEvent_t moments_done = nullptr;
+    if (same) {
+      // cells and positions first, on the library stream: the tile count
+      // (which reads only those) runs while momenta, weights and ids are
+      // still arriving over the transfer stream
+      for (int a = 0; a < 2; ++a)
         ZP_CU(cudaMemcpyAsync(dsts[a], srcs[a], sizeof(R) * n,
                               cudaMemcpyHostToDevice, stream_));
-      } else {
-        tmp.resize(n);
-        if (src->precision == ZPIC_FP64)
-          for (long long k = 0; k < n; ++k) tmp[k] = (R)((const double *)srcs[a])[k];
-        else
-          for (long long k = 0; k < n; ++k) tmp[k] = (R)((const float *)srcs[a])[k];
-        ZP_CU(cudaMemcpyAsync(dsts[a], tmp.data(), sizeof(R) * n,
-                              cudaMemcpyHostToDevice, stream_));
-        ZP_CU(cudaStreamSynchronize(stream_));
-      }
+      ZP_CU(cudaEventRecord(ev_pos_, stream_));
+      ZP_CU(cudaStreamWaitEvent(cpy_, ev_pos_, 0));
+      for (int a = 2; a < 6; ++a)
+        if (srcs[a])
+          ZP_CU(cudaMemcpyAsync(dsts[a], srcs[a], sizeof(R) * n,
+                                cudaMemcpyHostToDevice, cpy_));
+      if (src->id)
+        ZP_CU(cudaMemcpyAsync(stg_.id, src->id, 4 * n, cudaMemcpyHostToDevice, cpy_));
+      ZP_CU(cudaEventRecord(ev_mom_, cpy_));
+      moments_done = ev_mom_;
+    } else if (src->id) {
+      ZP_CU(cudaMemcpyAsync(stg_.id, src->id, 4 * n, cudaMemcpyHostToDevice, stream_));
+    }
+    std::vector<R> tmp;
+    for (int a = 0; a < 6 && !same; ++a) {
+      // other precision: converted on the host, one plane at a time
+      if (!srcs[a]) continue;
+      tmp.resize(n);
+      if (src->precision == ZPIC_FP64)
+        for (long long k = 0; k < n; ++k) tmp[k] = (R)((const double *)srcs[a])[k];
+      else
+        for (long long k = 0; k < n; ++k) tmp[k] = (R)((const float *)srcs[a])[k];
+      ZP_CU(cudaMemcpyAsync(dsts[a], tmp.data(), sizeof(R) * n,
+                            cudaMemcpyHostToDevice, stream_));
+      ZP_CU(cudaStreamSynchronize(stream_));
     }
     if (src->w) {
       S.sp[s].has_w = true;
@@ -586,7 +652,7 @@ class Batch : public BatchBase {
       set_deposit_units(S);
     }
     ZP_TRY(rebuild_species(si, s, n, src->w != nullptr, src->id != nullptr,
-                           true));
+                           true, moments_done));
     return ZPIC_OK;
   }
 
@@ -1053,10 +1119,14 @@ class Batch : public BatchBase {
         c = std::max<long long>(c, P.h_cap[t]);
         if (cnt[t] > P.h_cap[t]) c = std::max<long long>(c, 2LL * P.h_cap[t]);
       }
-      // a tile near one denser than the species' full density may be
-      // compressed next (a wake, a filament, a channel wall moving through
-      // the tiles): room for twice that density before it overflows
-      if (near[t] > nominal) c = std::max<long long>(c, 2LL * near[t]);
+      // a tile near one compressed beyond the species' full density plus
+      // the slack may be compressed next (a wake, a filament, a channel wall
+      // moving through the tiles): room for twice that density before it
+      // overflows.  Thermal scatter of a uniform plasma around its density
+      // stays below the threshold, so its capacities stay put and repeated
+      // uploads and re-sorts reuse the store's memory.
+      if (near[t] > nominal * (1.0 + slack))
+        c = std::max<long long>(c, 2LL * near[t]);
       c = (c + 31) / 32 * 32;
       if (tot + c > INT_MAX) return fail(ZPIC_ENOMEM, "species store exceeds 2^31");
       off[t] = (int)tot;
@@ -1071,12 +1141,17 @@ class Batch : public BatchBase {
     // each copy is one block of planes; a block that is large enough (and
     // not more than twice too large) is kept, so a re-sort or an upload of
     // the same size allocates nothing (the data it held is no longer needed:
-    // callers have moved the particles to the staging area)
+    // callers have moved the particles to the staging area).  A new block
+    // gets 1/8 headroom: tile capacities never shrink, so they creep up with
+    // the scatter of the counts between uploads, and that growth should not
+    // cost a free and an allocation of gigabytes each time.
+    const size_t block_new = (block + block / 8 + 255) & ~size_t(255);
     for (int b = 0; b < 2; ++b) {
       if (P.store[b].p && P.store[b].bytes >= block && P.store[b].bytes <= 2 * block)
         continue;
       dfree(P.store[b]);
-      if (!dalloc(P.store[b], block)) return fail(ZPIC_ENOMEM, "particle store");
+      if (!dalloc(P.store[b], block_new) && !dalloc(P.store[b], block))
+        return fail(ZPIC_ENOMEM, "particle store");
     }
     if (!P.off.p) {
       if (!dalloc(P.off, 4 * S.ntiles) || !dalloc(P.cap, 4 * S.ntiles) ||
@@ -1315,8 +1390,11 @@ class Batch : public BatchBase {
   }
 
   // Re-bins n staged particles into species s of sim si (new capacities).
+  // Bins n staged particles into the species' tiles.  ready: an event after
+  // which every staged plane other than cells and positions has arrived
+  // (those two are in place when this is called), or null.
   int rebuild_species(int si, int s, long long n, bool has_w, bool has_id,
-                      bool check) {
+                      bool check, cudaEvent_t ready = nullptr) {
     SimHost<R> &S = sims_[si];
     SpeciesHost<R> &P = S.sp[s];
     DevMem counts;
@@ -1340,6 +1418,7 @@ class Batch : public BatchBase {
                        full_tile_cap(nominal, slack, window_plasma(S, P))));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
+    if (ready) ZP_CU(cudaStreamWaitEvent(stream_, ready, 0));
     ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1, S.tx,
                                 S.ty, has_w ? 1 : 0, has_id ? 1 : 0, stream_));
     P.h_cnt = cnt;
@@ -1570,6 +1649,14 @@ class Batch : public BatchBase {
     }
     if (h_st_) cudaFreeHost(h_st_);
     h_st_ = nullptr;
+    if (cpy_) {
+      cudaStreamSynchronize(cpy_);
+      cudaStreamDestroy(cpy_);
+    }
+    cpy_ = nullptr;
+    if (ev_pos_) cudaEventDestroy(ev_pos_);
+    if (ev_mom_) cudaEventDestroy(ev_mom_);
+    ev_pos_ = ev_mom_ = nullptr;
     if (own_stream_) cudaStreamDestroy(own_stream_);
     own_stream_ = nullptr;
     stream_ = nullptr;
@@ -1578,6 +1665,10 @@ class Batch : public BatchBase {
   std::vector<SimHost<R>> sims_;
   std::unique_ptr<Allocator> alloc_;
   cudaStream_t own_stream_ = nullptr, stream_ = nullptr;
+  // second stream for host transfers that overlap the library stream's
+  // kernels (particle upload and download), with the events that order them
+  cudaStream_t cpy_ = nullptr;
+  cudaEvent_t ev_pos_ = nullptr, ev_mom_ = nullptr;
   size_t bytes_ = 0;
   DevMem st_mem_, sims_dev_, items_, yee_items_;
   DevMem ov_sim_, ov_sp_, ov_ix_, ov_iy_, ov_id_, ov_x_, ov_y_, ov_ux_, ov_uy_,
