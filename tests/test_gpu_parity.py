@@ -297,3 +297,38 @@ def test_field_energy_sum_is_compensated(precision):
     exact = 10 ** 18 + (nx * ny - 1)
     assert wB == 0.0
     assert wE / 0.125 == float(exact)
+
+
+@pytest.mark.parametrize("precision", [Z.FP32, Z.FP64])
+def test_particle_round_trip_through_host(precision):
+    # host transfers of the particle store: the download in tile ranges
+    # (any split, empty ranges included) equals the whole download, in the
+    # store's own precision and converted; an upload of what was downloaded
+    # gives back the same particles; weights and ids travel with them
+    nx, ny = 72, 40                      # ragged 16 x 16 tiles (5 x 3)
+    real = np.float64 if precision == Z.FP64 else np.float32
+    other = np.float32 if precision == Z.FP64 else np.float64
+    ld = P.random_particles(nx, ny, 30000, seed=9, umax=1.0, dtype=real)
+    ld["w"] = (0.5 + (np.arange(30000) % 7) / 7).astype(real)
+    cfg = cfg_for_loads(nx, ny, (0.1, 0.1), 0.07, [(-1.0, (4, 4))],
+                        precision=precision, tile=(16, 16))
+    gpu = Z.Sim(cfg)
+    gpu.set_particles(0, ld)
+    gpu.step(3)
+    a = gpu.particles(0)
+    assert len(a["id"]) == 30000
+    nt = gpu.info().ntiles_x * gpu.info().ntiles_y
+    for cuts in ((0, nt), (0, 1, 1, 7, nt), (0, 3, 4, nt - 1, nt)):
+        parts = [gpu.particles(0, tiles=(cuts[i], cuts[i + 1]))
+                 for i in range(len(cuts) - 1)]
+        for k in a:
+            np.testing.assert_array_equal(
+                np.concatenate([p_[k] for p_ in parts]), a[k])
+    b = gpu.particles(0, dtype=other)
+    for k in a:
+        np.testing.assert_array_equal(b[k], a[k].astype(b[k].dtype))
+    gpu.set_particles(0, a)
+    c = H.by_id(gpu.particles(0))
+    a = H.by_id(a)
+    for k in a:
+        np.testing.assert_array_equal(c[k], a[k])
