@@ -302,6 +302,18 @@ def timed_steps(sim, stream, steps, torch):
     return e0.elapsed_time(e1)
 
 
+def stage_split(sim, steps):
+    """CUDA-event time per stage and step over `steps` further steps run
+    with per-stage events (outside the timed region)."""
+    sim.profile_enable(True)
+    sim.profile_read(reset=True)
+    sim.step(steps)
+    sim.sync()
+    prof = sim.profile_read(reset=True)
+    sim.profile_enable(False)
+    return {k: v[0] / max(v[1], 1) for k, v in prof.items()}
+
+
 def base_line(metric_value, ms, args, dtype, config, **extra):
     out = {"metric": "particle-steps/s", "value": metric_value,
            "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
@@ -342,6 +354,7 @@ def batch_workload(args, rank, world):
         n += sum(inf.n_particles[:inf.n_species])
     barrier(world)
     ms_b = timed_steps(batch, stream, args.steps, torch)
+    split = stage_split(batch, args.steps)
     del batch
     sims = [Z.Sim(c) for c in cfgs]
     for sm in sims:
@@ -374,7 +387,8 @@ def batch_workload(args, rank, world):
             n_gpus=world, scaling="strong",
             per_sim_launches={"value": value_s,
                               "ms_per_step": ms_s_max / args.steps},
-            batched_over_per_sim=ms_s_max / ms_b_max)))
+            batched_over_per_sim=ms_s_max / ms_b_max,
+            kernels_ms_next_steps=split)))
     else:
         all_sum(float(n), world)
 
@@ -420,14 +434,16 @@ def other_workload(args):
         ms = timed_steps(sim, stream, args.steps, torch)
         info = sim.info()
         n1 = sum(info.n_particles[:info.n_species])
+        r1 = info.resorts
         ps = 0.5 * (n0 + n1) * args.steps
         print(json.dumps(base_line(
             ps / (ms / 1e3), ms, args, "f32",
             {"workload": desc, "nx": cfg.nx, "ny": cfg.ny,
              "particles_start": int(n0), "particles_end": int(n1),
              "steps_before_timing": warm},
-            resorts_in_timed_region=info.resorts - r0,
-            step_after=int(info.step))))
+            resorts_in_timed_region=r1 - r0,
+            step_after=int(info.step),
+            kernels_ms_next_steps=stage_split(sim, args.steps))))
         return
     if args.workload == "tiles":
         # the autotuner's tile-size sweep for the workload classes (each on

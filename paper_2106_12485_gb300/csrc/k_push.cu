@@ -711,8 +711,9 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
 
 // The work of one CTA on one tile; CUR = step & 1 selects the field and
 // particle copies, as a compile-time value so that every descriptor access
-// has a constant offset.  kSpec: the single-simulation 16 x 16 FP32 kernel,
-// whose species loops are also specialised on layout and boundary.
+// has a constant offset.  kSpec: the 16 x 16 FP32 kernels (one simulation
+// or a batch), whose species loops are also specialised on layout and
+// boundary.
 template <typename R, bool kBatch, int TXC, int TYC, int CUR>
 __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
                                           const int tile, const int step,
@@ -720,7 +721,7 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
                                           const OverflowDev<R> &ovf,
                                           unsigned char *smem_raw,
                                           int *s_slots, double *red) {
-  constexpr bool kSpec = sizeof(R) == 4 && !kBatch && TXC == 16 && TYC == 16;
+  constexpr bool kSpec = sizeof(R) == 4 && TXC == 16 && TYC == 16;
   const int nx = S.nx, ny = S.ny, ld = S.ld;
   const int TX = TXC > 0 ? TXC : S.tx, TY = TYC > 0 ? TYC : S.ty;
   const int open_x = S.open_x, nsp = S.nsp;

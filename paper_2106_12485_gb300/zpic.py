@@ -489,6 +489,11 @@ class Batch:
         check(lib().zpic_batch_profile_enable(self.h, 1 if on else 0),
               "zpic_batch_profile_enable")
 
+    def profile_read(self, reset=True):
+        """Per-stage device time of the batch (read through a member's view,
+        which shares the batch's timers)."""
+        return self.sim(0).profile_read(reset)
+
     def close(self):
         if self.h:
             lib().zpic_batch_destroy(self.h)
