@@ -367,6 +367,45 @@ def test_energy_bounded_thermal_plasma():
         nx * ny * 0.01 * 0.5 * 3 * 0.01, rel=0.05)  # ~ n m u_th^2 * 3/2 * area
 
 
+def test_field_energy_closed_form():
+    """W_E = 1/2 sum E^2 dx dy and W_B = 1/2 sum B^2 dx dy over the cells,
+    every component counted: a uniform component, a single cell of another
+    and a single negative cell of the third, with dx != dy."""
+    nx, ny, dx, dy = 6, 5, 0.3, 0.2
+    sim = O.Sim(nx, ny, dx, dy, 0.1)
+    z = np.zeros((ny, nx))
+    ey, ez, bz = z.copy(), z.copy(), z.copy()
+    ey[1, 2] = 2.0
+    ez[4, 5] = -3.0
+    bz[0, 0] = 4.0
+    for k, v in (("ex", np.ones((ny, nx))), ("ey", ey), ("ez", ez),
+                 ("bx", np.full((ny, nx), 0.5)), ("by", z), ("bz", bz)):
+        sim.set_field(k, v)
+    wE, wB = sim.field_energy()
+    assert wE == pytest.approx(0.5 * (nx * ny * 1.0 + 4.0 + 9.0) * dx * dy,
+                               rel=1e-15)
+    assert wB == pytest.approx(0.5 * (nx * ny * 0.25 + 16.0) * dx * dy,
+                               rel=1e-15)
+
+
+def test_kinetic_energy_closed_form():
+    """K_s = sum m_p (gamma - 1) dx dy with m_p = q_p / (q/m) and gamma of
+    the momentum after the push; with no fields the push leaves u as it
+    is, so hand-picked momenta give exact values: u = (3/4, 0, 0) has
+    gamma - 1 = 1/4, u = (0, 0.6, 0.8) has gamma = sqrt 2.  Two species with
+    different q0, q/m and weights are kept apart."""
+    dx, dy = 0.25, 0.5
+    a = O.Species(-2.0, -0.5, [1, 3], [2, 0], [0.5, 0.25], [0.5, 0.75],
+                  [0.75, 0.0], [0.0, 0.6], [0.0, 0.8], w=[1.0, 2.0])
+    b = O.Species(1.0, 0.125, [2], [1], [0.5], [0.5], [0.0], [0.0], [0.75])
+    sim = O.Sim(8, 4, dx, dy, 0.05, species=[a, b])
+    _, wE, wB, kin = sim.step()
+    # m_p: 0.5 * 1 / 2 = 0.25 and 0.5 * 2 / 2 = 0.5; 0.125 / 1
+    assert kin[0] == pytest.approx((0.25 * 0.25 + 0.5 * (np.sqrt(2) - 1))
+                                   * dx * dy, rel=1e-14)
+    assert kin[1] == pytest.approx(0.125 * 0.25 * dx * dy, rel=1e-14)
+
+
 # ----------------------------------------------------------------- laser --
 
 def test_laser_propagates_forward_at_group_velocity():
