@@ -188,12 +188,17 @@ __device__ __forceinline__ void dep_seg(const TileJ<R> &J, int JW, int JP,
 // The path of a particle in its start cell's frame, from (x, y) to
 // (x1, y1), split at the cell faces it crosses: cross iff the end lies at or
 // beyond a face (axis_cross); sx, sy = path parameters where it meets the x
-// face xb and the y face yb (1 when that axis is not crossed); s1 = min,
-// s2 = max, an exact tie counting as x first.  Segment 1 lies in the start
-// cell, segment 2 in the cell entered at s1, segment 3 (two crossings) in
-// the final cell; each is written in its own cell's frame and the last one
-// ends at the stored offsets (xf, yf).  The same code serves the particle
-// loop and the deferred segments, so both see the same rounding.
+// face xb and the y face yb (1 when that axis is not crossed, at most 1
+// otherwise: the fast division may round a quotient of numbers within an
+// ulp of each other above 1).  The order of the crossings is decided only
+// between axes that are crossed: a path that crosses one face is cut there
+// even when it ends within rounding of it (s = 1), and when both are
+// crossed an exact tie counts as x first.  s1 = the first crossing, s2 =
+// the second (1 when there is none).  Segment 1 lies in the start cell,
+// segment 2 in the cell entered at s1, segment 3 (two crossings) in the
+// final cell; each is written in its own cell's frame and the last one ends
+// at the stored offsets (xf, yf).  The same code serves the particle loop
+// and the deferred segments, so both see the same rounding.
 template <typename R>
 struct PathSplit {
   int di, dj;     // cell steps
@@ -211,9 +216,9 @@ __device__ __forceinline__ PathSplit<R> split_path(R x, R y, R x1, R y1) {
   p.dj = axis_cross(y1, p.yf);
   p.xb = p.di > 0 ? R(1) : R(0);
   p.yb = p.dj > 0 ? R(1) : R(0);
-  p.sx = p.di ? fdiv<R>(p.xb - x, x1 - x) : R(1);
-  p.sy = p.dj ? fdiv<R>(p.yb - y, y1 - y) : R(1);
-  p.xfirst = p.sx <= p.sy;
+  p.sx = p.di ? fmin(fdiv<R>(p.xb - x, x1 - x), R(1)) : R(1);
+  p.sy = p.dj ? fmin(fdiv<R>(p.yb - y, y1 - y), R(1)) : R(1);
+  p.xfirst = p.di != 0 && (p.dj == 0 || p.sx <= p.sy);
   p.s1 = p.xfirst ? p.sx : p.sy;
   p.s2 = p.xfirst ? p.sy : p.sx;
   p.x_sx_y = y + p.sx * (y1 - y);
@@ -510,6 +515,12 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   if (threadIdx.x == 0) {
     T.s_slots[0] = 0;
     T.s_slots[1] = 0;
+    // report which compiled form pushes this species (read first: the bit
+    // is set once, by the first tile that runs it)
+    const int form = kSpec ? (kOpen ? ZPIC_PUSH_PLAIN_OPEN
+                                    : ZPIC_PUSH_PLAIN_PERIODIC)
+                           : ZPIC_PUSH_GENERIC;
+    if (!(__ldcg(S.variants + s) & form)) atomicOr(S.variants + s, form);
   }
   __syncthreads();  // also: coefficient tile ready, J tile zeroed
   int n_removed = 0;

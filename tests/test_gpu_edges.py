@@ -65,6 +65,65 @@ def test_crafted_edge_particles_match_oracle(precision, tol):
                   (g["iy"] < ny))
 
 
+def face_landings(nx, ny, dtype, d=0.1, dt=0.07,
+                  speeds=(0.13, 0.17, 0.21, 0.25, 0.3, 0.34, 0.38, 0.42,
+                          0.47, 0.51, 0.55, 0.6)):
+    """Particles whose straight path ends within a few units of the last
+    place of a cell face, crossing only that face: along y forward (end at
+    1 - k ulp .. 1 + k ulp), along y backward (end at -k ulp .. +k ulp), and
+    the same along x, for several speeds (so that the quotients of the path
+    split round both ways).  u is exact and the fields are zero, so the end
+    is start + dt u / (gamma d), which the sweep of start offsets walks
+    across the face one unit at a time."""
+    one = dtype(1)
+    rows = []
+    k = 0
+    for u0 in speeds:
+        c = dtype(dt * u0 / np.sqrt(1.0 + u0 * u0) / d)  # cells per step
+        for axis in (0, 1):
+            for sign in (1, -1):
+                v = dtype(one - c if sign > 0 else c)
+                for _ in range(8):               # walk back 8 units
+                    v = np.nextafter(v, dtype(0))
+                for _ in range(20):
+                    ix, iy = k % nx, (k // nx) % ny
+                    off = (v, dtype(0.5)) if axis == 0 else (dtype(0.5), v)
+                    u = (sign * u0, 0.0) if axis == 0 else (0.0, sign * u0)
+                    rows.append((ix, iy, off[0], off[1], u[0], u[1]))
+                    v = np.nextafter(v, one)
+                    k += 1
+    n = len(rows)
+    return {"ix": np.array([r[0] for r in rows], np.int32),
+            "iy": np.array([r[1] for r in rows], np.int32),
+            "x": np.array([r[2] for r in rows], dtype),
+            "y": np.array([r[3] for r in rows], dtype),
+            "ux": np.array([r[4] for r in rows], dtype),
+            "uy": np.array([r[5] for r in rows], dtype),
+            "uz": np.zeros(n, dtype), "w": np.ones(n, dtype),
+            "id": np.arange(n, dtype=np.int32)}
+
+
+@pytest.mark.parametrize("precision,tol", [(Z.FP32, 1e-4), (Z.FP64, 1e-10)])
+def test_face_landings_within_rounding(precision, tol):
+    # a path that crosses one face and ends within rounding of it is split
+    # at that face only (the crossing order matters only when both faces
+    # are crossed); the current of every particle must match the oracle's
+    nx, ny = 48, 40
+    dt = np.float64 if precision == Z.FP64 else np.float32
+    cfg = Z.config(nx, ny, (nx * 0.1, ny * 0.1), 0.07,
+                   [Z.species(-1.0, (1, 1), profile=Z.PROFILE_NONE)],
+                   precision=precision, track_ids=True)
+    ld = face_landings(nx, ny, dt)
+    gpu, orc = H.make_pair(cfg, [ld])
+    gpu.step(1)
+    orc.step(1)
+    assert gpu.num_particles(0) == orc.species[0].n == len(ld["ix"])
+    H.compare_fields(gpu, orc, tol, names=("jx", "jy", "jz"))
+    H.compare_particles(gpu, orc, 0, nx, ny, tol)
+    g = gpu.particles(0)
+    assert np.all((g["x"] >= 0) & (g["x"] < 1) & (g["y"] >= 0) & (g["y"] < 1))
+
+
 def test_empty_species_next_to_a_full_one():
     nx, ny = 48, 32
     cfg = Z.config(nx, ny, (nx * 0.1, ny * 0.1), 0.07,
