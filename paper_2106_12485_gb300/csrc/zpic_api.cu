@@ -725,6 +725,8 @@ class Batch : public BatchBase {
     }
     o->resorts = resorts_;
     o->device_bytes = bytes_;
+    ZP_CU(cudaMemcpy(o->push_variants, S.dev.variants,
+                     sizeof(int) * kMaxSpecies, cudaMemcpyDeviceToHost));
     return ZPIC_OK;
   }
 
@@ -977,7 +979,7 @@ class Batch : public BatchBase {
     D.hist_skip = 0;
     if (!dalloc(S.energy_rows, sizeof(double) * (2 * (size_t)S.ny + 2)))
       return fail(ZPIC_ENOMEM, "energy scratch");
-    if (!dalloc(S.small, sizeof(int) * (3 + 2 * kMaxSpecies)))
+    if (!dalloc(S.small, sizeof(int) * (3 + 3 * kMaxSpecies)))
       return fail(ZPIC_ENOMEM, "counters");
     ZP_CU(cudaMemsetAsync(S.small.p, 0, S.small.bytes, stream_));
     D.hist_n = (int *)S.small.p;
@@ -985,6 +987,7 @@ class Batch : public BatchBase {
     D.removed = (int *)S.small.p + 2;
     D.ob_need = (int *)S.small.p + 2 + kMaxSpecies;
     D.eticket = (int *)S.small.p + 2 + 2 * kMaxSpecies;
+    D.variants = (int *)S.small.p + 3 + 2 * kMaxSpecies;
 
     // species: initial per-tile counts from the profile, then capacities
     S.sp.resize(c.n_species);

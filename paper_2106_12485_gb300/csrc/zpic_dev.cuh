@@ -131,6 +131,8 @@ struct SimDev {
   int *ob_need;                // [kMaxSpecies] most leavers one tile had in
                                // a step when that exceeded its outbox
                                // (0: none); the re-sort grows the outbox
+  int *variants;               // [kMaxSpecies] bits of the push-kernel forms
+                               // that ran for the species (ZPIC_PUSH_*)
   SpeciesDev<R> sp[kMaxSpecies];
 };
 

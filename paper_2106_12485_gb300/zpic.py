@@ -26,6 +26,7 @@ FIELD_IDS = {"ex": EX, "ey": EY, "ez": EZ, "bx": BX, "by": BY, "bz": BZ,
 PROFILE_NONE, PROFILE_UNIFORM, PROFILE_SLAB, PROFILE_RAMP = 0, 1, 2, 3
 TRACK_IDS = 1
 FILTER_J = 2
+PUSH_GENERIC, PUSH_PLAIN_PERIODIC, PUSH_PLAIN_OPEN = 1, 2, 4
 
 
 class zpic_species(C.Structure):
@@ -78,7 +79,8 @@ class zpic_info(C.Structure):
                 ("n_shift", C.c_int32), ("n_species", C.c_int),
                 ("n_particles", C.c_int64 * MAX_SPECIES),
                 ("capacity", C.c_int64 * MAX_SPECIES),
-                ("resorts", C.c_int32), ("device_bytes", C.c_size_t)]
+                ("resorts", C.c_int32), ("device_bytes", C.c_size_t),
+                ("push_variants", C.c_int32 * MAX_SPECIES)]
 
 
 class zpic_state(C.Structure):

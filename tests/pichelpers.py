@@ -25,6 +25,19 @@ def oracle_species(ld, qm, ppc, cap=None):
                      cap=cap)
 
 
+def oracle_sim(cfg, loads, window=None, cap_extra=0):
+    """The oracle on `loads` (one per species of cfg)."""
+    species = []
+    for s, ld in enumerate(loads):
+        sp = cfg.species[s]
+        species.append(oracle_species(ld, sp.q_over_m, sp.ppc_x * sp.ppc_y,
+                                      cap=len(ld["ix"]) + cap_extra))
+    dx, dy = cfg.box_x / cfg.nx, cfg.box_y / cfg.ny
+    return O.Sim(cfg.nx, cfg.ny, dx, dy, cfg.dt, open_x=bool(cfg.bc_x),
+                 species=species, window=window,
+                 filter_j=bool(cfg.flags & Z.FILTER_J))
+
+
 def make_pair(cfg, loads, fields=None, window=None, cap_extra=0):
     """GPU sim (cfg, particles from `loads`) and oracle sim on the same
     inputs.  cfg's species give q/m and ppc; their profile should be NONE so
@@ -135,3 +148,63 @@ def continuity_residual(jx, jy, rho0, rho1, dx, dy, dt):
     div = (jx - np.roll(jx, 1, axis=1)) / dx + (jy - np.roll(jy, 1, axis=0)) / dy
     drho = (rho1 - rho0) / dt
     return np.linalg.norm(drho + div) / np.linalg.norm(drho)
+
+
+def strip_layout(ld):
+    """The load without weight and id planes: uploaded to a simulation
+    without ZPIC_TRACK_IDS it gives the plain particle layout (the one the
+    16x16 FP32 kernel is specialised for); every weight of these loads is 1,
+    so the particles are the same."""
+    assert np.all(np.asarray(ld["w"]) == 1)
+    return {k: v for k, v in ld.items() if k not in ("w", "id")}
+
+
+def tile_counts_of(st, tx, ty, ntx, nty):
+    """Particles per tile (index ty * ntx + tx) of a particle set."""
+    t = (np.asarray(st["iy"]) // ty) * ntx + np.asarray(st["ix"]) // tx
+    return np.bincount(t, minlength=ntx * nty)
+
+
+def cic_map(nx, ny, st, weight, open_x=False):
+    """Sum of `weight` per particle spread to the nodes with CIC weights
+    (FP64, numpy); weight = the particle's charge gives the charge density,
+    charge x u_k a momentum density."""
+    ix = np.asarray(st["ix"], np.int64)
+    iy = np.asarray(st["iy"], np.int64)
+    x = np.asarray(st["x"], np.float64)
+    y = np.asarray(st["y"], np.float64)
+    w = np.asarray(weight, np.float64)
+    out = np.zeros(nx * ny)
+    for di, wx in ((0, 1 - x), (1, x)):
+        for dj, wy in ((0, 1 - y), (1, y)):
+            i = ix + di
+            j = (iy + dj) % ny
+            keep = (i >= 0) & (i < nx) if open_x else np.ones(i.shape, bool)
+            i = i % nx
+            np.add.at(out, (j * nx + i)[keep], (w * wx * wy)[keep])
+    return out.reshape(ny, nx)
+
+
+def fluct_rel_l2(a, b):
+    """Relative L2 of a - b against the fluctuation of b about its mean (a
+    uniform plasma's density is dominated by its mean, which hides errors in
+    the positions)."""
+    b = np.asarray(b, np.float64)
+    d = np.linalg.norm(np.asarray(a, np.float64) - b)
+    return d / max(np.linalg.norm(b - b.mean()), 1e-300)
+
+
+def match_particles(g, o, scale_u=1.0):
+    """Pairs the particles of two sets without ids: each particle of g with
+    its nearest neighbour of o in (global x, global y, u / scale_u).  Returns
+    (index into o for every particle of g, distance); the caller checks that
+    the pairing is one-to-one and the distances are small."""
+    from scipy.spatial import cKDTree
+    def pts(s):
+        return np.stack([np.asarray(s["ix"], np.float64) + s["x"],
+                         np.asarray(s["iy"], np.float64) + s["y"],
+                         np.asarray(s["ux"], np.float64) / scale_u,
+                         np.asarray(s["uy"], np.float64) / scale_u,
+                         np.asarray(s["uz"], np.float64) / scale_u], axis=1)
+    d, k = cKDTree(pts(o)).query(pts(g))
+    return k, d
