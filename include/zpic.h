@@ -174,6 +174,15 @@ typedef struct {
     double kin[ZPIC_MAX_SPECIES];
 } zpic_energy_rec;
 
+/* Forms of the particle kernel (zpic_info.push_variants, one bit each):
+ * the 16x16-tile FP32 kernel is compiled separately for species that store
+ * neither weights nor ids (the plain layout), with a periodic or an open x
+ * boundary; every other species runs the form that reads its layout at run
+ * time. */
+#define ZPIC_PUSH_GENERIC 1
+#define ZPIC_PUSH_PLAIN_PERIODIC 2
+#define ZPIC_PUSH_PLAIN_OPEN 4
+
 /* Layout and state summary of a simulation. */
 typedef struct {
     int nx, ny, ld;             /* ld = padded row length of field arrays */
@@ -187,6 +196,10 @@ typedef struct {
     int64_t capacity[ZPIC_MAX_SPECIES];
     int32_t resorts;            /* full re-sorts done (overflow recovery)  */
     size_t device_bytes;        /* device memory held                     */
+    int32_t push_variants[ZPIC_MAX_SPECIES]; /* ZPIC_PUSH_* bits of the
+                                   particle-kernel forms that ran for each
+                                   species since creation (recorded by the
+                                   kernel itself)                         */
 } zpic_info;
 
 /* Run state beyond fields and particles, for checkpoint / restart. */
@@ -213,17 +226,27 @@ typedef struct zpic_batch zpic_batch;
  * fields (Sec. 4.1).  *out receives the handle.  cfg is copied. */
 int zpic_create(const zpic_config *cfg, zpic_sim **out);
 
-/* Frees a simulation created by zpic_create (not a batch view). */
+/* Frees a simulation created by zpic_create (not a batch view); the
+ * device memory of its fields and tile stores goes back to the allocator. */
 int zpic_destroy(zpic_sim *sim);
 
-/* Enqueues n time steps (each: push+deposit, Yee, tile migration, window)
- * on the handle's stream and returns.  Errors of earlier steps found at
- * the last synchronisation are returned here. */
+/* Enqueues n time steps on the handle's stream and returns.  One step is
+ * the PIC cycle of Sec. 2.2 (Fig. 1): interpolation of E, B at the
+ * particles, Boris push, charge-conserving deposition, Yee field advance;
+ * then the hand-over of particles that crossed into a neighbouring tile
+ * (the region hand-over of Sec. 3.2, at most one cell per step) and the
+ * moving-window shift of Sec. 4.1.  Errors of earlier steps found at the
+ * last synchronisation are returned here (ZPIC_EOVERFLOW, ZPIC_ENAN,
+ * ZPIC_ETIMEOUT sticky; ZPIC_ECUDA on a failed launch). */
 int zpic_step(zpic_sim *sim, int n);
 
 /* Waits for all enqueued steps; recovers from tile-capacity overflow by
  * re-sorting with more capacity and re-running the steps that were held
- * back.  Returns the device status. */
+ * back (a tile, like a region of Sec. 3.2, holds the particles of its
+ * cells; one that receives more than its room parks them until the host
+ * re-sorts).  Returns the device status: ZPIC_OK, or the sticky
+ * ZPIC_EOVERFLOW (storage exhausted after re-sorting), ZPIC_ENAN,
+ * ZPIC_ETIMEOUT, ZPIC_ECUDA. */
 int zpic_sync(zpic_sim *sim);
 
 /* Uses `stream` (a cudaStream_t) for all later work of the handle.  NULL
@@ -242,11 +265,17 @@ int zpic_get_fields_f64(zpic_sim *sim, int which, double *dst, size_t cap);
 int zpic_set_fields_f64(zpic_sim *sim, int which, const double *src,
                         size_t n);
 
-/* Number of particles of a species (synchronises). */
+/* Number of particles of a species (synchronises); particles leave only
+ * through an open x boundary and enter only with the moving window's new
+ * column (Sec. 4.1). */
 int zpic_num_particles(zpic_sim *sim, int species, int64_t *n);
 
-/* Copies the particles of a species into dst (tile order).  ZPIC_ECAP if
- * dst->cap is too small; dst->n receives the count. */
+/* Copies the particles of a species into dst (tile order): global cell
+ * (ix, iy), offsets (x, y) in [0, 1), u = gamma v at the half step of the
+ * leapfrog (Sec. 2.2), weight and id when the arrays are given.  The
+ * arrays are caller-owned host memory of dst->cap elements; ZPIC_ECAP if
+ * that is too small, ZPIC_EINVAL for NULL arrays or a bad species;
+ * *n_written receives the count. */
 int zpic_get_particles(zpic_sim *sim, int species, const zpic_particles *dst,
                        size_t *n_written);
 
@@ -262,7 +291,10 @@ int zpic_get_particles_tiles(zpic_sim *sim, int species, int tile_begin,
  * 0 <= iy < ny and offsets in [0, 1) (ZPIC_EINVAL otherwise). */
 int zpic_set_particles(zpic_sim *sim, int species, const zpic_particles *src);
 
-/* Copies the energy history (one record per energy_every steps).  With
+/* Copies the energy history (one record per energy_every steps): field
+ * energies and kinetic energy per species, summed on the device in
+ * compensated FP64 (the validation quantity of Sec. 4.2).  dst is
+ * caller-owned host memory of cap records; ZPIC_ECAP if too small.  With
  * dst == NULL and cap == 0 only *n_written is set (size query). */
 int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
                 size_t *n_written);
@@ -275,35 +307,40 @@ int zpic_energy(zpic_sim *sim, zpic_energy_rec *dst, size_t cap,
 int zpic_field_energy(zpic_sim *sim, double *wE, double *wB);
 
 /* The same energies as zpic_field_energy, for callers that cannot
- * allocate device memory when they need them (code running while a stream
- * is captured into a CUDA graph, real-time loops that must not wait on an
- * allocator, hosts that give the library a fixed memory budget).  The paper
- * has no counterpart; this entry point allocates nothing.
+ * allocate device memory when they need them (real-time loops that must not
+ * wait on an allocator, hosts that give the library a fixed memory budget).
+ * The paper has no counterpart; this entry point allocates nothing.
  *   ex .. bz: device arrays (FP32) of ny rows of ld >= nx values, owned by
- *             the caller; nx*ny cells of size dx*dy are summed.
+ *             the caller; nx*ny cells of size dx*dy are summed (values in
+ *             the ld - nx padding columns are not read).
  *   out:      host array of 2 doubles: 1/2 sum E^2 dx dy, 1/2 sum B^2 dx dy.
  *   stream:   cudaStream_t to run on (NULL: the default stream); the call
  *             returns after the stream has finished the work.
  * Scratch: a static device array built into the library for at most 65536
  * rows (1 MiB + 16 bytes, held by every GPU that loads the library until
- * exit); ny > 65536 returns ZPIC_EINVAL.  The first call on each device looks
- * up that array's address with the device current, so make the first call
- * on a device before capturing any stream.  All calls share the array:
- * calls that overlap on the GPU (different streams, or several host
- * threads) race and may return wrong sums.  Nothing in it needs clearing:
- * each call writes every value it reads.  Errors: ZPIC_EINVAL (NULL pointer,
- * bad sizes), ZPIC_ECUDA (no device, launch or copy failure). */
+ * exit); ny > 65536 returns ZPIC_EINVAL.  The first call on each device
+ * (and the first after the device's context changed, e.g. after
+ * cudaDeviceReset) looks up that array's address with the device current,
+ * so make the first call on a device before capturing any stream.  All
+ * calls share the array: calls that overlap on the GPU (different streams,
+ * or several host threads) race and may return wrong sums.  Nothing in it
+ * needs clearing: each call writes every value it reads.  Errors:
+ * ZPIC_EINVAL (NULL pointer, bad sizes), ZPIC_ECUDA (no device, launch or
+ * copy failure). */
 int zpic_field_energy_noalloc_f32(const float *ex, const float *ey,
                                   const float *ez, const float *bx,
                                   const float *by, const float *bz, int nx,
                                   int ny, int ld, double dx, double dy,
                                   double *out, void *stream);
 
-/* Fills *info (synchronises). */
+/* Fills *info (synchronises): grid, tile decomposition (the regions of
+ * Sec. 3.2), counts, capacities and the particle-kernel forms that ran.
+ * ZPIC_EINVAL for NULL. */
 int zpic_get_info(zpic_sim *sim, zpic_info *info);
 
-/* Per-tile particle counts of a species, tile index ty*ntiles_x + tx, in
- * the order zpic_get_particles writes them. */
+/* Per-tile particle counts of a species (the regions of Sec. 3.2), tile
+ * index ty*ntiles_x + tx, in the order zpic_get_particles writes them.
+ * dst: caller-owned, cap >= ntiles (ZPIC_ECAP otherwise). */
 int zpic_get_tile_counts(zpic_sim *sim, int species, int32_t *dst,
                          size_t cap);
 
@@ -367,8 +404,14 @@ int zpic_profile_read(zpic_sim *sim, char *names, size_t name_len,
 
 /* Batched simulations (independent; same precision): one launch per stage
  * advances all of them over a (simulation, tile) work list, captured in a
- * CUDA graph.  zpic_batch_sim gives a view handle for the getters; views
- * are freed with the batch. */
+ * CUDA graph.  Each member runs the step of Sec. 2.2 exactly as it would
+ * alone (bitwise the same in FP32); the work list takes the place of the
+ * paper's task scheduler (Sec. 3.2: regions as tasks, over-decomposition
+ * of Sec. 4.3), ordered longest first.  zpic_batch_create copies the n
+ * configurations (ZPIC_EINVAL if they differ in precision); zpic_batch_step
+ * and zpic_batch_sync behave like zpic_step and zpic_sync for all members;
+ * zpic_batch_sim gives a view handle for the getters (views are freed with
+ * the batch; zpic_destroy on a view is ZPIC_EINVAL). */
 int zpic_batch_create(const zpic_config *cfgs, int n, zpic_batch **out);
 int zpic_batch_step(zpic_batch *b, int n);
 int zpic_batch_sync(zpic_batch *b);

@@ -1,13 +1,13 @@
 // noalloc.cu -- field energies computed without allocating any device memory.
 //
 // Some callers cannot allocate device memory at the moment they want this
-// diagnostic: code running while a CUDA stream is being captured into a
-// graph (cudaMalloc is not allowed during capture), real-time loops that
-// must never stall on an allocator, and host applications that give this
-// library a fixed memory budget or their own pool and forbid it to grow.
-// zpic_field_energy_noalloc_f32 serves them: it runs the same reduction as
-// zpic_field_energy, on device arrays the caller already owns, and keeps
-// its scratch space in an array compiled into the library.
+// diagnostic: real-time loops that must never stall on an allocator, and
+// host applications that give this library a fixed memory budget or their
+// own pool and forbid it to grow.  zpic_field_energy_noalloc_f32 serves
+// them: it runs the same reduction as zpic_field_energy, on device arrays
+// the caller already owns, and keeps its scratch space in an array compiled
+// into the library.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -28,11 +28,52 @@ constexpr int kMaxRows = 65536;
 static __device__ __align__(256) double g_energy_scratch[2 * kMaxRows + 2];
 
 // Device address of g_energy_scratch per device.  In host code the symbol
-// name is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached here.
+// name is only a host-side stand-in, so the address is looked up with the
+// device current and cached here, together with the id of the context it
+// belongs to: after cudaDeviceReset (or when the host makes another context
+// current on the device) the array lives at a new address, and the lookup
+// runs again.
 constexpr int kMaxDevices = 64;
-double *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  double *p = nullptr;
+  unsigned long long ctx_id = 0;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mu;
+
+// Id of the calling thread's current context (0 when none is current yet),
+// through the driver entry points the runtime hands out (no link against
+// the driver library).
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000,
+                                         cudaEnableDefault, &qa) ==
+            cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000,
+                                         cudaEnableDefault, &qb) ==
+            cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      get_current = (GetCurrent)a;
+      get_id = (GetId)b;
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int scratch_for_current_device(double **out) {
   int dev = -1;
@@ -44,7 +85,9 @@ int scratch_for_current_device(double **out) {
   if (dev < 0 || dev >= kMaxDevices)
     return zp::set_last_error(ZPIC_ENOTSUP, "device index beyond 63");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchAddr &a = g_scratch_addr[dev];
+  const unsigned long long ctx = current_context_id();
+  if (!a.p || ctx == 0 || ctx != a.ctx_id) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_energy_scratch);
     if (e != cudaSuccess || !p) {
@@ -52,9 +95,10 @@ int scratch_for_current_device(double **out) {
       return zp::set_last_error(
           ZPIC_ECUDA, "cudaGetSymbolAddress of the built-in scratch failed");
     }
-    g_scratch_addr[dev] = (double *)p;
+    a.p = (double *)p;
+    a.ctx_id = current_context_id();  // current now, if it was not before
   }
-  *out = g_scratch_addr[dev];
+  *out = a.p;
   return ZPIC_OK;
 }
 
