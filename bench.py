@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the FP64 form, the batched-vs-per-sim "
+                    "comparison and the precision errors against the oracle")
     ap.add_argument("--cpu-sample", type=int, default=512,
                     help="cells per side of the oracle sample")
     ap.add_argument("--workload", default="uniform",
@@ -214,25 +217,40 @@ def algorithmic_bytes(n_particles, n_cells, real_bytes):
 
 # ---------------------------------------------------------- CPU oracle ----
 
-def oracle_sample(cells, ppc, steps, nthreads):
+def oracle_sample(cells, ppc, steps, nthreads, keep=False):
     """Times the FP64 oracle on a cells x cells periodic box of the same
     plasma (both species, same ppc and u_th).  Returns (ps/s, n_particles,
-    seconds)."""
+    seconds), and with keep=True also the oracle (advanced `steps` steps
+    from step 0; an untimed warm-up runs on a copy) and its loads."""
     from oracle import oracle as O
     from synthetic import plasma as P
-    sps = []
-    for s, qm in enumerate((-1.0, 1.0)):
-        ld = P.plasma_load(cells, cells, ppc, ppc, species=s,
-                           u_th=(0.1, 0.1, 0.1), dtype=np.float64)
-        sps.append(O.Species(qm, (1 if qm > 0 else -1) / ppc ** 2, ld["ix"],
-                             ld["iy"], ld["x"], ld["y"], ld["ux"], ld["uy"],
-                             ld["uz"], w=ld["w"], ids=ld["id"]))
-    sim = O.Sim(cells, cells, 0.1, 0.1, 0.07, species=sps)
-    n = sum(s.n for s in sps)
-    sim.step(1, nthreads=nthreads)     # warm-up (page faults, threads)
+
+    def make():
+        lds, sps = [], []
+        for s, qm in enumerate((-1.0, 1.0)):
+            ld = P.plasma_load(cells, cells, ppc, ppc, species=s,
+                               u_th=(0.1, 0.1, 0.1), dtype=np.float32)
+            lds.append(ld)
+            f = {k: np.asarray(ld[k], np.float64)
+                 for k in ("x", "y", "ux", "uy", "uz", "w")}
+            sps.append(O.Species(qm, (1 if qm > 0 else -1) / ppc ** 2,
+                                 ld["ix"], ld["iy"], f["x"], f["y"], f["ux"],
+                                 f["uy"], f["uz"], w=f["w"], ids=ld["id"]))
+        return O.Sim(cells, cells, 0.1, 0.1, 0.07, species=sps), lds, \
+            sum(s.n for s in sps)
+
+    sim, lds, n = make()
+    if keep:
+        warm, _, _ = make()
+        warm.step(1, nthreads=nthreads)   # warm-up (page faults, threads)
+        del warm
+    else:
+        sim.step(1, nthreads=nthreads)
     t0 = time.perf_counter()
     sim.step(steps, nthreads=nthreads)
     dt = time.perf_counter() - t0
+    if keep:
+        return n * steps / dt, n, dt, sim, lds
     return n * steps / dt, n, dt
 
 
@@ -260,13 +278,17 @@ def reference_arm(args, rank, world):
     v = n * args.steps / dt
     sample = ("%dx%d periodic box of the same plasma (%d particles), %d "
               "oracle steps" % (cells, cells, n, args.steps))
+    # the config is the box the oracle ran: a sample of the GPU workload
+    # (same plasma, cell size, time step and particles per cell), not the
+    # full grid
+    config = sampled_config(args, cells, n)
     print(json.dumps({
         "impl": "reference", "metric": "particle-steps/s", "value": v,
         "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args),
+        "config": config,
         "cpu_baseline": {"value": v, "unit": "particle-steps/s",
                          "cores": nthreads, "kind": "oracle",
                          "sample": sample},
@@ -285,6 +307,166 @@ def workload_config(args):
             "particles": 2 * args.nx * args.ny * ppc * ppc,
             "precision": args.precision,
             "l2": "inputs larger than L2 (particle store >> 129 MB)"}
+
+
+def sampled_config(args, cells, n):
+    """Config of a timed sample of the workload: a cells x cells periodic
+    box of the same plasma."""
+    full = workload_config(args)
+    return {"workload": "uniform thermal plasma %dx%d, e-/e+ %dx%d ppc "
+                        "each, u_th 0.1, dx=dy=0.1, dt=0.07, periodic "
+                        "(sample of the %dx%d workload)" %
+                        (cells, cells, args.ppc, args.ppc, args.nx, args.ny),
+            "nx": cells, "ny": cells, "species": 2,
+            "ppc_per_species": args.ppc * args.ppc, "particles": int(n),
+            "precision": "fp64", "sampled": True,
+            "sampled_from": full["workload"]}
+
+
+# ------------------------------------------------- secondary figures ----
+
+def fp32_over_fp64(args, stream, torch, fp32_value, steps=5):
+    """The all-FP64 GPU form on the same workload and time step: its
+    particle-steps/s over `steps` CUDA-event-timed steps (after 2 warm-up
+    steps) and the ratio FP32 / FP64.  Both forms share dt, so their
+    energy-conservation error is the scheme's (equal drift, measured by
+    --workload precision)."""
+    from paper_2106_12485_gb300 import workloads as W
+    from paper_2106_12485_gb300 import zpic as Z
+    cfg = W.precision_study(args.nx, args.ny, ppc=(args.ppc, args.ppc),
+                            precision=Z.FP64, energy_every=1)
+    sim = Z.Sim(cfg)
+    sim.set_stream(stream.cuda_stream)
+    inf = sim.info()
+    n = int(sum(inf.n_particles[:2]))
+    sim.step(2)
+    sim.sync()
+    ms = timed_steps(sim, stream, steps, torch)
+    e = sim.energy()
+    tot = [r[1] + r[2] + sum(r[3]) for r in e]
+    drift = max(abs(t - tot[0]) for t in tot) / tot[0]
+    del sim
+    v64 = n * steps / (ms / 1e3)
+    return {"fp64_value": v64, "fp64_ms_per_step": ms / steps,
+            "fp64_steps": steps, "fp64_energy_drift": drift,
+            "ratio": fp32_value / v64}
+
+
+def batched_over_per_sim(args, stream, torch, steps=10):
+    """The batched sweep (256 independent simulations, one persistent
+    launch per stage, captured in a CUDA graph) against the same simulations
+    stepped one by one: aggregate particle-steps/s of both and the ratio."""
+    from paper_2106_12485_gb300 import workloads as W
+    from paper_2106_12485_gb300 import zpic as Z
+    from synthetic import plasma as P
+    cfgs = W.batch_sweep(P.batch_specs(256))
+    batch = Z.Batch(cfgs)
+    batch.set_stream(stream.cuda_stream)
+    batch.step(3)
+    batch.sync()
+    n = 0
+    for i in range(len(cfgs)):
+        inf = batch.sim(i).info()
+        n += sum(inf.n_particles[:inf.n_species])
+    ms_b = timed_steps(batch, stream, steps, torch)
+    del batch
+    sims = [Z.Sim(c) for c in cfgs]
+    for sm in sims:
+        sm.set_stream(stream.cuda_stream)
+        sm.step(3)
+    for sm in sims:
+        sm.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for sm in sims:
+            sm.step(1)
+    for sm in sims:
+        sm.sync()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    del sims
+    return {"sims": len(cfgs), "particles": int(n), "steps": steps,
+            "batched_value": n * steps / (ms_b / 1e3),
+            "per_sim_value": n * steps / (ms_s / 1e3),
+            "ratio": ms_s / ms_b}
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def precision_vs_oracle(orc, loads, cells, steps, stream):
+    """Error of the FP32 and the all-FP64 GPU forms against the FP64 oracle
+    `orc` (already advanced `steps` steps from `loads`, a cells x cells box
+    of the workload's plasma): relative L2 of each field, of the particle
+    displacements and momenta (particles paired by id), and of the total
+    energy at every step."""
+    from paper_2106_12485_gb300 import zpic as Z
+    FIELDS = ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz")
+    x0 = []
+    for ld in loads:
+        o = np.argsort(ld["id"], kind="stable")
+        x0.append((ld["ix"][o] + ld["x"][o].astype(np.float64),
+                   ld["iy"][o] + ld["y"][o].astype(np.float64)))
+    tot_o = np.array([h[1] + h[2] + float(np.sum(h[3])) for h in orc.history])
+    out = {}
+    for name, prec, dt in (("fp32", Z.FP32, np.float32),
+                           ("fp64", Z.FP64, np.float64)):
+        ppc = int(round(np.sqrt(len(loads[0]["ix"]) / cells ** 2)))
+        sps = [Z.species(qm, (ppc, ppc), profile=Z.PROFILE_NONE)
+               for qm in (-1.0, 1.0)]
+        cfg = Z.config(cells, cells, (cells * 0.1, cells * 0.1), 0.07, sps,
+                       precision=prec, track_ids=True, energy_every=1)
+        sim = Z.Sim(cfg)
+        sim.set_stream(stream.cuda_stream)
+        for s, ld in enumerate(loads):
+            sim.set_particles(s, {k: (v.astype(dt) if v.dtype.kind == "f"
+                                      else v) for k, v in ld.items()})
+        sim.step(steps)
+        f = {k: rel_l2(sim.field(k), orc.f[k]) for k in FIELDS}
+        pos, mom = 0.0, 0.0
+        for s in range(2):
+            st = sim.particles(s)
+            og = np.argsort(st["id"], kind="stable")
+            ost = orc.species[s].state()
+            oo = np.argsort(ost["id"], kind="stable")
+            if not np.array_equal(st["id"][og], ost["id"][oo]):
+                pos = mom = float("inf")
+                break
+            rx, ry = x0[s]
+            gx = st["ix"][og] + st["x"][og].astype(np.float64)
+            gy = st["iy"][og] + st["y"][og].astype(np.float64)
+            ox = ost["ix"][oo] + ost["x"][oo]
+            oy = ost["iy"][oo] + ost["y"][oo]
+            wrap = lambda d: (d + cells / 2) % cells - cells / 2  # noqa: E731
+            num = np.hypot(wrap(gx - ox), wrap(gy - oy))
+            den = np.hypot(wrap(ox - rx), wrap(oy - ry))
+            pos = max(pos, float(np.linalg.norm(num) / np.linalg.norm(den)))
+            gu = np.stack([st[k][og] for k in ("ux", "uy", "uz")])
+            ou = np.stack([ost[k][oo] for k in ("ux", "uy", "uz")])
+            mom = max(mom, rel_l2(gu, ou))
+        e = sim.energy()
+        tot_g = np.array([r[1] + r[2] + sum(r[3]) for r in e])
+        del sim
+        out[name] = {"fields_rel_l2_max": max(f.values()),
+                     "fields_rel_l2": f,
+                     "displacement_rel_l2": pos, "momentum_rel_l2": mom,
+                     "total_energy_rel_err_max":
+                         float(np.max(np.abs(tot_g - tot_o) / tot_o)),
+                     "energy_drift": float(np.max(np.abs(tot_g - tot_g[0]))
+                                           / tot_g[0])}
+    out["oracle_energy_drift"] = float(np.max(np.abs(tot_o - tot_o[0]))
+                                       / tot_o[0])
+    out["steps"] = steps
+    out["box"] = "%dx%d periodic, same plasma as the workload" % (cells,
+                                                                  cells)
+    return out
 
 
 # --------------------------------------------------------------- main ----
@@ -619,15 +801,32 @@ def main():
                        "on the host clock"}
         del pinned
 
+    # ---- secondary figures: FP32 vs FP64, batched vs per-sim ----------
+    second = {}
+    if world == 1 and not args.no_secondary:
+        del sim
+        torch.cuda.synchronize()
+        if prec == Z.FP32:
+            second["fp32_over_fp64"] = fp32_over_fp64(args, stream, torch,
+                                                      value)
+        second["batched_over_per_sim"] = batched_over_per_sim(args, stream,
+                                                              torch)
+
     # ---- CPU oracle baseline (rank 0 only) ----------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         # all host threads (the particle-decomposed mode of Sec. 3.1) on a
-        # box of cpu_sample^2 cells, and one thread on a quarter of it
+        # box of cpu_sample^2 cells, and one thread on a quarter of it.  The
+        # timed oracle run (20 steps from the seeded load) is also the
+        # reference of the precision errors of both GPU forms at step 20.
         nthreads = os.cpu_count() or 1
-        steps_mt = 10
-        v, n, secs = oracle_sample(args.cpu_sample, args.ppc, steps_mt,
-                                   nthreads)
+        steps_mt = 20
+        v, n, secs, orc, lds = oracle_sample(args.cpu_sample, args.ppc,
+                                             steps_mt, nthreads, keep=True)
+        if prec == Z.FP32 and not args.no_secondary:
+            second["precision_vs_oracle"] = precision_vs_oracle(
+                orc, lds, args.cpu_sample, steps_mt, stream)
+        del orc, lds
         c1 = max(args.cpu_sample // 2, 8)
         v1, n1, secs1 = oracle_sample(c1, args.ppc, 2, 1)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": nthreads,
@@ -662,6 +861,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
         }
+        out.update(second)
         print(json.dumps(out))
 
 

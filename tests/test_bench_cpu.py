@@ -21,17 +21,42 @@ def test_algorithmic_bytes():
         44.28, abs=0.01)
 
 
-def test_traffic_follows_the_committed_summary(tmp_path, monkeypatch):
+def test_traffic_follows_the_summary_of_the_same_kernel(tmp_path,
+                                                        monkeypatch):
     n, cells = 1000, 10
-    got = bench.measured_traffic("fp32", n, cells)
-    assert got is not None and 40 * n < got < 46 * n
+    fake = tmp_path / "traffic.txt"
+    fake.write_text("# comment\npush_deposit sha=%s precision=fp32 "
+                    "dram_bytes_per_particle=43.3 source=x\n"
+                    % bench.push_kernel_hash())
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(fake))
+    assert bench.measured_traffic("fp32", n, cells) == pytest.approx(43.3 * n)
     assert bench.measured_traffic("fp64", n, cells) is None
     # a summary taken with another kernel source is not used
-    fake = tmp_path / "traffic.txt"
     fake.write_text("push_deposit sha=0000000000000000 precision=fp32 "
                     "dram_bytes_per_particle=43.3 source=x\n")
-    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(fake))
     assert bench.measured_traffic("fp32", n, cells) is None
+
+
+def test_committed_traffic_summary_is_well_formed():
+    # the committed line parses; it is used only while its sha matches
+    with open(bench.TRAFFIC_PATH) as f:
+        rows = [ln.split() for ln in f if ln.startswith("push_deposit ")]
+    assert rows
+    for r in rows:
+        kv = dict(t.split("=", 1) for t in r[1:])
+        assert len(kv["sha"]) == 16 and kv["precision"] in ("fp32", "fp64")
+        assert 0 < float(kv["dram_bytes_per_particle"]) < 200
+
+
+def test_sampled_config_names_the_box_it_ran():
+    class A:
+        nx = ny = 2048
+        ppc = 8
+        precision = "fp32"
+    c = bench.sampled_config(A(), 256, 2 * 256 * 256 * 64)
+    assert (c["nx"], c["ny"], c["sampled"]) == (256, 256, True)
+    assert c["particles"] == 2 * 256 * 256 * 64
+    assert "256x256" in c["workload"] and "2048x2048" in c["sampled_from"]
 
 
 def test_workload_config_names_the_workload():
