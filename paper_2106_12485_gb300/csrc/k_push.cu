@@ -18,10 +18,13 @@
 //     paths of particles that cross a face wait in a per-warp queue and
 //     their remaining segments are deposited 32 at a time;
 //  3. writes particles that stay in the tile to the tile's segment of the
-//     other copy of the store (each warp claims a run of slots with one
-//     shared-memory atomic, so warps never wait for each other) and
-//     particles that leave to the tile's outbox; particles leaving an open
-//     boundary are dropped;
+//     other copy of the store in their input order: each warp owns a
+//     contiguous range of the segment and compacts its stayers to the start
+//     of that range, and the CTA then moves the last particles into the
+//     gaps (close_gaps), so warps never wait for each other and the order of
+//     the store (neighbouring slots in neighbouring cells after a re-sort)
+//     carries over from step to step; particles that leave go to the tile's
+//     outbox, particles leaving an open boundary are dropped;
 //  4. adds the shared J tile (interior and guard cells) to the global J,
 //     one reduction per cell (periodic images folded here); in FP32 the
 //     global J is an int64 fixed-point sum, so the result does not depend
@@ -445,6 +448,57 @@ __device__ __noinline__ void park_leaver(const SpeciesDev<R> &P,
   atomicMin(&st->err_step, step);
 }
 
+// After the species' particle loop: warp w kept s_stay[w] particles at the
+// start of its range [r0_w, r1_w) of the output segment (the same slot split
+// as the loop's), so the tile's kept particles are not yet contiguous.  The
+// kept particles that lie at or beyond slot `kept` (their total) move, last
+// ones first into the first gaps, into the gaps below `kept`; both lists
+// are walked in slot order, so the result does not depend on timing.  Few
+// particles leave a tile per step, so few move; they were written moments
+// ago by this CTA and are read through L2.  Returns `kept`.
+template <typename R>
+__device__ __forceinline__ int close_gaps(const Planes<R> &O, int base, int n,
+                                          int *sg, bool has_w, bool has_id) {
+  // sg[0, kPW): particles kept per warp; sg[kPW, 5 kPW): per range, the
+  // first gap slot, the gap slots below `kept`, the first kept particle at
+  // or beyond `kept` and their number
+  int *gap_lo = sg + kPW, *gap_n = sg + 2 * kPW;
+  int *src_lo = sg + 3 * kPW, *src_n = sg + 4 * kPW;
+  const int NC = (n + 31) >> 5;
+  int kept = 0;
+  for (int w = 0; w < kPW; ++w) kept += sg[w];
+  if (threadIdx.x < kPW) {
+    const int w = threadIdx.x;
+    const int r0 = (w * NC / kPW) * 32;
+    const int r1 = min(((w + 1) * NC / kPW) * 32, n);
+    const int e = r0 + sg[w];
+    gap_lo[w] = e;
+    gap_n[w] = max(0, min(r1, kept) - e);
+    src_lo[w] = max(r0, kept);
+    src_n[w] = max(0, e - src_lo[w]);
+  }
+  __syncthreads();
+  int m = 0;
+  for (int w = 0; w < kPW; ++w) m += gap_n[w];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    int kg = k, wg = 0;
+    while (kg >= gap_n[wg]) kg -= gap_n[wg++];
+    int ks = k, ws = 0;
+    while (ks >= src_n[ws]) ks -= src_n[ws++];
+    const size_t d = (size_t)base + gap_lo[wg] + kg;
+    const size_t q = (size_t)base + src_lo[ws] + ks;
+    O.cell[d] = __ldcg(O.cell + q);
+    O.x[d] = __ldcg(O.x + q);
+    O.y[d] = __ldcg(O.y + q);
+    O.ux[d] = __ldcg(O.ux + q);
+    O.uy[d] = __ldcg(O.uy + q);
+    O.uz[d] = __ldcg(O.uz + q);
+    if (has_w) O.w[d] = __ldcg(O.w + q);
+    if (has_id) O.id[d] = __ldcg(O.id + q);
+  }
+  return kept;
+}
+
 // Shared-memory layout of the push kernel for tx x ty tiles (byte offsets):
 // the coefficient tile (6 components x (tx+1)(ty+1) cells), the current
 // tile (3 planes of (tx+3)(ty+3) values, 8 bytes each: two int32 words in
@@ -486,6 +540,7 @@ struct TileCtx {
   R dt_dx, dt_dy;
   bool do_energy;
   int *s_slots;
+  int *s_stay;  // particles each warp kept (kPW), then close_gaps scratch
   double *red;
 };
 
@@ -513,7 +568,6 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   const Coef4<R> *cBx = T.cf + 3 * CP, *cBy = T.cf + 4 * CP,
                  *cBz = T.cf + 5 * CP;
   if (threadIdx.x == 0) {
-    T.s_slots[0] = 0;
     T.s_slots[1] = 0;
     // report which compiled form pushes this species (read first: the bit
     // is set once, by the first tile that runs it)
@@ -528,10 +582,19 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   R kin = R(0);
 
   // warps work independently on chunks of 32 particles: no block barrier
-  // inside the loop; each warp claims its output slots with one atomic.
-  // Chunk jc of warp `warp` starts at particle warp * 32 + jc * kPT.
+  // inside the loop.  Warp `warp` owns the contiguous slots [r0, r1) (its
+  // share of the tile's chunks) and writes the particles that stay in the
+  // tile to the start of the same range of the other copy, in their input
+  // order (no atomic, no wait on other warps); close_gaps then moves the
+  // last particles of the tile into the gaps the leavers left.  A store in
+  // which neighbouring slots hold neighbouring cells keeps that order from
+  // step to step, and so do its bank-conflict-free gathers and deposits.
   constexpr int kS = Ring<R>::kStages;
-  const int nch = n > warp * 32 ? (n - warp * 32 + kPT - 1) / kPT : 0;
+  const int NC = (n + 31) >> 5;
+  const int ca = warp * NC / kPW, cb = (warp + 1) * NC / kPW;
+  const int nch = cb - ca;
+  const int r0 = ca * 32;
+  int n_stay = 0;  // particles this warp has kept (warp-uniform)
   const unsigned sbytes = Ring<R>::stage_bytes(has_w, has_id);
   const unsigned stg0 = smem_addr(T.stages) + warp * kS * sbytes;
   RingLane rl;
@@ -541,12 +604,12 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
     for (int jc = 0; jc < kS - 1; ++jc) {
       if (jc < nch)
         ring_issue(rl, stg0 + ((g + jc) % kS) * sbytes,
-                   base + warp * 32 + jc * kPT);
+                   base + r0 + jc * 32);
       cp_async_commit();
     }
   }
   for (int jc = 0; jc < nch; ++jc, ++g) {
-    const int c0 = warp * 32 + jc * kPT;
+    const int c0 = r0 + jc * 32;
     // lanes past the end repeat the last particle with zero weight: they
     // run the same instructions, deposit nothing and store nothing
     const bool valid = c0 + lane < n;
@@ -559,7 +622,7 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
       __syncwarp();
       if (jc + kS - 1 < nch)
         ring_issue(rl, stg0 + ((g + kS - 1) % kS) * sbytes,
-                   c0 + base + (kS - 1) * kPT);
+                   c0 + base + (kS - 1) * 32);
       cp_async_commit();
       cp_async_wait<kS - 1>();  // this lane's pieces of chunk jc landed
       __syncwarp();             // ... and every other lane's
@@ -677,19 +740,17 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
     const bool leave = valid && !removed && !inside;
     if (valid && removed) ++n_removed;
 
-    // ---- output: stayers to this tile's segment of the other copy,
-    // leavers (global cell) to the tile's outbox ----
+    // ---- output: stayers to this warp's range of the other copy, in input
+    // order; leavers (global cell) to the tile's outbox ----
     const unsigned bs = __ballot_sync(0xffffffffu, stay);
     const unsigned bl = __ballot_sync(0xffffffffu, leave);
-    int sb = 0, lb = 0;
-    if (lane == 0) {
-      if (bs) sb = atomicAdd(&T.s_slots[0], __popc(bs));
-      if (bl) lb = atomicAdd(&T.s_slots[1], __popc(bl));
+    int lb = 0;
+    if (bl) {  // warp-uniform
+      if (lane == 0) lb = atomicAdd(&T.s_slots[1], __popc(bl));
+      lb = __shfl_sync(0xffffffffu, lb, 0);
     }
-    sb = __shfl_sync(0xffffffffu, sb, 0);
-    lb = __shfl_sync(0xffffffffu, lb, 0);
     if (stay) {
-      const int d = base + sb + __popc(bs & lt);
+      const int d = base + r0 + n_stay + __popc(bs & lt);
       __stcs(O.cell + d, local_cell(nlx, nly));
       __stcs(O.x + d, ps.xf);
       __stcs(O.y + d, ps.yf);
@@ -703,18 +764,22 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
                   nix, niy, ps.xf, ps.yf, ux, uy, uz, w, pid,
                   has_w && O.w != nullptr, has_id && O.id != nullptr);
     }
+    n_stay += __popc(bs);
   }
   // segments still waiting in the warp's queue
   __syncwarp();
   if (lane < qtail - qhead)
     queue_take(T.q, T.jt, JW, JP, (qhead + lane) & (kQ - 1), qx0, qy0);
+  if (lane == 0) T.s_stay[warp] = n_stay;
   if (n_removed) atomicAdd(&S.removed[s], n_removed);
   if (T.do_energy)
     block_sum_store<R>((double)kin,
                        &S.part_kin[(size_t)s * S.ntx * S.nty + T.tile], T.red);
-  __syncthreads();
+  __syncthreads();  // every warp's stayers written, s_stay complete
+  const int kept = close_gaps(O, base, n, T.s_stay, has_w && O.w != nullptr,
+                              has_id && O.id != nullptr);
   if (threadIdx.x == 0) {
-    P.cnt[T.tile] = T.s_slots[0];
+    P.cnt[T.tile] = kept;
     P.ob_cnt[T.tile] = min(T.s_slots[1], P.ob_cap);
     if (T.s_slots[1] > P.ob_cap) atomicMax(&S.ob_need[s], T.s_slots[1]);
   }
@@ -731,7 +796,8 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
                                           BatchStatus *st,
                                           const OverflowDev<R> &ovf,
                                           unsigned char *smem_raw,
-                                          int *s_slots, double *red) {
+                                          int *s_slots, int *s_stay,
+                                          double *red) {
   constexpr bool kSpec = sizeof(R) == 4 && TXC == 16 && TYC == 16;
   const int nx = S.nx, ny = S.ny, ld = S.ld;
   const int TX = TXC > 0 ? TXC : S.tx, TY = TYC > 0 ? TYC : S.ty;
@@ -774,6 +840,7 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
   T.dt_dx = S.dt_dx;
   T.dt_dy = S.dt_dy;
   T.s_slots = s_slots;
+  T.s_stay = s_stay;
   T.red = red;
 
   // ---- stage 0: fields of the tile + one guard cell, coefficient form ----
@@ -867,7 +934,8 @@ __global__ void __launch_bounds__(kPT, sizeof(R) == 4 ? kPushCtasF32 : 2)
                         BatchStatus *st,
                         const __grid_constant__ OverflowDev<R> ovf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_slots[2];  // stayers written, leavers written
+  __shared__ int s_slots[2];  // [1]: leavers written to the outbox
+  __shared__ int s_stay[5 * kPW];
   __shared__ double red[kPW];
   __shared__ int s_item;
 
@@ -897,10 +965,10 @@ __global__ void __launch_bounds__(kPT, sizeof(R) == 4 ? kPushCtasF32 : 2)
     }
     if (step & 1)
       push_tile<R, kBatch, TXC, TYC, 1>(S, it.x, it.y, step, st, ovf,
-                                        smem_raw, s_slots, red);
+                                        smem_raw, s_slots, s_stay, red);
     else
       push_tile<R, kBatch, TXC, TYC, 0>(S, it.x, it.y, step, st, ovf,
-                                        smem_raw, s_slots, red);
+                                        smem_raw, s_slots, s_stay, red);
     __syncthreads();  // shared memory is reused by the next item
   }
 }
