@@ -148,6 +148,16 @@ typedef struct {
                                    configuration's class, else 16         */
     int flags;                  /* ZPIC_TRACK_IDS | ZPIC_FILTER_J         */
     double capacity_slack;      /* spare tile capacity fraction; 0: 0.25  */
+    int sort_every;             /* re-sort every tile's particles into
+                                   cell-interleaved order every k steps
+                                   (k >= 1); -1: never; 0: the interval
+                                   zpic_autotune chose for this
+                                   configuration's class, else never      */
+    int push_ctas_per_sm;       /* resident particle-kernel CTAs per SM
+                                   (1..8, capped at what fits); 0: the
+                                   number zpic_autotune chose for this
+                                   configuration's class, else all that
+                                   fit                                     */
 } zpic_config;
 
 /* Particle arrays for get/set.  Real arrays (x .. w) hold float when
@@ -200,6 +210,9 @@ typedef struct {
                                    particle-kernel forms that ran for each
                                    species since creation (recorded by the
                                    kernel itself)                         */
+    int32_t sort_every;         /* re-sort interval in use (-1: never)    */
+    int32_t push_ctas_per_sm;   /* particle-kernel CTAs per SM in use     */
+    int32_t sorts;              /* cell-order re-sorts done on the device */
 } zpic_info;
 
 /* Run state beyond fields and particles, for checkpoint / restart. */
@@ -392,6 +405,31 @@ int zpic_autotune(const zpic_config *cfg, int steps, int *best_tile_x,
 /* Writes up to cap candidate tile sizes (x, y pairs) to tile_xy and returns
  * how many candidates there are. */
 int zpic_autotune_candidates(int *tile_xy, int cap);
+
+/* Settings of the particle kernel that zpic_autotune_all chooses. */
+typedef struct {
+    int tile_x, tile_y;         /* tile size (the region of Sec. 3.2)     */
+    int push_ctas_per_sm;       /* resident particle-kernel CTAs per SM:
+                                   the tiles in flight per SM, the GPU
+                                   counterpart of the regions per core of
+                                   the over-decomposition study (Sec. 4.3) */
+    int sort_every;             /* cell-order re-sort interval, -1: never */
+    double ms_per_step;         /* the chosen setting on the reduced copy */
+} zpic_tuning;
+
+/* Tunes tile size, resident CTAs per SM and re-sort interval for cfg's
+ * class, one after the other, on the reduced copy zpic_autotune uses: the
+ * tile candidates of zpic_autotune_candidates at `steps` timed steps, then
+ * 1..3 CTAs per SM (1..2 in FP64) at the best tile, then re-sort intervals
+ * -1 (never), 10, 20, 40 at the best of both, each timed over 80 steps
+ * after 40 (the particle order of a new simulation decays over tens of
+ * steps, so shorter windows favour no re-sort unduly).  The choice is kept
+ * for the class and used by zpic_create for settings left at 0.
+ * ms_per_candidate[k] (k < cap, may be NULL) receives each timing in that
+ * order (negative: could not run); *n_candidates their number.  Errors as
+ * for zpic_autotune. */
+int zpic_autotune_all(const zpic_config *cfg, int steps, zpic_tuning *best,
+                      double *ms_per_candidate, int cap, int *n_candidates);
 
 /* Kernel timing: when enabled, zpic_step launches kernels one by one and
  * records a CUDA event pair around each launch on the handle's stream.

@@ -1,14 +1,19 @@
-// autotune.cu -- host autotuner of the particle tile size.
+// autotune.cu -- host autotuner of the particle kernel's settings.
 //
 // The tile is the unit of work of the push (one CTA per tile) and of the
 // particle sort, so its size trades shared-memory staging and guard-cell
 // overhead (small tiles) against CTA count and load balance (large tiles,
-// few particles). zpic_autotune times one configuration for each candidate
-// tile size on a copy reduced to at most 1024 x 1024 cells (same cell size,
-// time step, species, densities and momenta; profiles, window and laser
-// placed at the same distance from the right edge), keeps the fastest per
-// configuration class, and zpic_create uses that choice when a
-// configuration asks for tile size 0 (default 16 x 16 otherwise).
+// few particles).  The resident CTAs per SM set how many tiles are in
+// flight on an SM (the paper's regions per core, Sec. 4.3).  The cell-order
+// re-sort interval trades the cost of rewriting the store against the
+// faster particle kernel on a store whose neighbouring slots hold
+// neighbouring cells.  zpic_autotune times the tile-size candidates;
+// zpic_autotune_all times them, then the CTA counts at the best tile, then
+// the re-sort intervals at the best of both.  Both run on a copy reduced to
+// at most 1024 x 1024 cells (same cell size, time step, species, densities
+// and momenta; profiles, window and laser placed at the same distance from
+// the right edge), keep the fastest per configuration class, and
+// zpic_create uses the choice for settings a configuration leaves at 0.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +40,7 @@ constexpr int kMaxSide = 1024;
 
 std::mutex g_mu;
 std::map<std::string, std::pair<int, int>> g_tuned;
+std::map<std::string, zpic_tuning> g_tuned_all;
 
 // The class of a configuration: what decides the best tile size is the
 // precision, the particles per cell of each species (the work per tile),
@@ -78,14 +84,14 @@ zpic_config reduced(const zpic_config &c) {
   return r;
 }
 
-// Host wall time of `steps` steps after a warm-up (ms per step), or a
-// negative value if the candidate cannot run (e.g. too large for shared
-// memory).
-double time_candidate(const zpic_config &r, int steps) {
+// Host wall time of `steps` steps after `warm` warm-up steps (ms per
+// step), or a negative value if the candidate cannot run (e.g. too large
+// for shared memory).
+double time_candidate(const zpic_config &r, int steps, int warm = 3) {
   zpic_sim *h = nullptr;
   if (zpic_create(&r, &h) != ZPIC_OK) return -1.0;
   double ms = -1.0;
-  if (zpic_step(h, 3) == ZPIC_OK && zpic_sync(h) == ZPIC_OK) {
+  if (zpic_step(h, warm) == ZPIC_OK && zpic_sync(h) == ZPIC_OK) {
     const auto t0 = std::chrono::steady_clock::now();
     if (zpic_step(h, steps) == ZPIC_OK && zpic_sync(h) == ZPIC_OK) {
       const auto t1 = std::chrono::steady_clock::now();
@@ -100,9 +106,22 @@ const int kCand[][2] = {{16, 16}, {8, 8}, {12, 12}, {24, 24}, {32, 32},
                         {32, 16}, {16, 32}};
 constexpr int kNCand = sizeof(kCand) / sizeof(kCand[0]);
 
+const int kCtaCand[] = {1, 2, 3};
+const int kSortCand[] = {-1, 10, 20, 40};
+constexpr int kSortWarm = 40, kSortSteps = 80;
+
 }  // namespace
 
 namespace zp {
+// The settings zpic_autotune_all chose for c's class, if it has run.
+bool tuned_setting(const zpic_config &c, zpic_tuning *t) {
+  std::lock_guard<std::mutex> g(g_mu);
+  auto it = g_tuned_all.find(class_key(c));
+  if (it == g_tuned_all.end()) return false;
+  *t = it->second;
+  return true;
+}
+
 // The tuned tile size of c's class, if zpic_autotune has run for it.
 bool tuned_tile(const zpic_config &c, int *tx, int *ty) {
   std::lock_guard<std::mutex> g(g_mu);
@@ -158,6 +177,85 @@ int zpic_autotune(const zpic_config *cfg, int steps, int *best_tile_x,
   *best_tile_x = bx;
   *best_tile_y = by;
   return status;
+}
+
+int zpic_autotune_all(const zpic_config *cfg, int steps, zpic_tuning *best,
+                      double *ms_per_candidate, int cap, int *n_candidates) {
+  if (!cfg || !best) return zp::set_last_error(ZPIC_EINVAL, "NULL argument");
+  if (steps < 1 || steps > 10000)
+    return zp::set_last_error(ZPIC_EINVAL, "steps out of range");
+  const int n_cta = cfg->precision == ZPIC_FP64 ? 2 : 3;
+  const int n_sort = (int)(sizeof(kSortCand) / sizeof(kSortCand[0]));
+  const int total = kNCand + n_cta + n_sort;
+  if (n_candidates) *n_candidates = total;
+  int k_out = 0;
+  auto record = [&](double ms) {
+    if (ms_per_candidate && k_out < cap) ms_per_candidate[k_out] = ms;
+    ++k_out;
+  };
+  zpic_config base = reduced(*cfg);
+  base.sort_every = -1;
+  base.push_ctas_per_sm = 0;
+  // tile size
+  double bt = -1.0;
+  int bx = 16, by = 16;
+  for (int k = 0; k < kNCand; ++k) {
+    zpic_config r = base;
+    r.tile_x = kCand[k][0];
+    r.tile_y = kCand[k][1];
+    const double ms = time_candidate(r, steps);
+    record(ms);
+    if (ms > 0 && (bt < 0 || ms < bt)) {
+      bt = ms;
+      bx = kCand[k][0];
+      by = kCand[k][1];
+    }
+  }
+  if (bt < 0)
+    return zp::set_last_error(ZPIC_ECUDA, "no tile size candidate could run");
+  base.tile_x = bx;
+  base.tile_y = by;
+  // resident CTAs per SM
+  double bc = -1.0;
+  int ctas = 0;
+  for (int k = 0; k < n_cta; ++k) {
+    zpic_config r = base;
+    r.push_ctas_per_sm = kCtaCand[k];
+    const double ms = time_candidate(r, steps);
+    record(ms);
+    if (ms > 0 && (bc < 0 || ms < bc)) {
+      bc = ms;
+      ctas = kCtaCand[k];
+    }
+  }
+  base.push_ctas_per_sm = ctas;
+  // re-sort interval, over a window long enough for the order to decay
+  double bs = -1.0;
+  int sort = -1;
+  for (int k = 0; k < n_sort; ++k) {
+    zpic_config r = base;
+    r.sort_every = kSortCand[k];
+    const double ms = time_candidate(r, kSortSteps, kSortWarm);
+    record(ms);
+    if (ms > 0 && (bs < 0 || ms < bs)) {
+      bs = ms;
+      sort = kSortCand[k];
+    }
+  }
+  zpic_tuning t{};
+  t.tile_x = bx;
+  t.tile_y = by;
+  t.push_ctas_per_sm = ctas;
+  t.sort_every = sort;
+  t.ms_per_step = bs;
+  {
+    const std::string key = class_key(*cfg);
+    std::lock_guard<std::mutex> g(g_mu);
+    g_tuned[key] = {bx, by};
+    g_tuned_all[key] = t;
+  }
+  *best = t;
+  return ZPIC_OK;
 }
 
 int zpic_autotune_candidates(int *tile_xy, int cap) {

@@ -602,6 +602,11 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) {
     if (owner && S.moving_window && shift_due(S, step, *S.n_shift))
       *S.n_shift += 1;
+    if (owner && sort_due(S, step)) {
+      // the re-sort wrote the other copy of the particle store
+      *S.pswap ^= 1;
+      *S.sorts += 1;
+    }
     __threadfence();
     const int t = atomicAdd(&st->blocks_done, 1);
     if (t == (int)gridDim.x - 1) {

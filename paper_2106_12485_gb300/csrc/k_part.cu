@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(kPT_MIG)
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
 
-  const int nxt = (step + 1) & 1;  // the copy the push kernel just wrote
+  // the copy the push kernel just wrote
+  const int nxt = ((step + 1) & 1) ^ *S.pswap;
   for (int s = 0; s < S.nsp; ++s) {
     const SpeciesDev<R> &P = S.sp[s];
     const Planes<R> &O = P.buf[nxt];
@@ -371,6 +372,217 @@ cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
   init_load_kernel<R><<<ntiles, kThreads, 0, stream>>>(sim_dev, lp);
   return cudaGetLastError();
 }
+
+// ---- cell-order re-sort ----------------------------------------------------
+//
+// Every sort_every steps, after the migration, each tile's particles are
+// rewritten into the other copy of the store in cell-interleaved order: the
+// first particle of every cell (cells in row-major order within the tile),
+// then the second of every cell that holds two or more, and so on.  Thirty-
+// two neighbouring slots then hold particles of thirty-two different,
+// neighbouring cells, whose coefficient gathers and current atomics in the
+// particle kernel fall on different shared-memory banks; that kernel keeps
+// the store order from step to step and the order erodes only as particles
+// drift between cells.  The end-of-step kernel then makes the sorted copy
+// the current one.
+//
+// Per tile and species: a histogram of the cells; for every rank r a bit
+// mask of the cells that hold more than r particles, with prefix counts of
+// its 32-cell words; a particle of cell c that takes rank r (in the order
+// the slots are read) goes to slot T(r) + (cells before c that hold more
+// than r particles), T(r) being the number of particles of rank below r.
+// Ranks are handed out chunk by chunk of slots (a barrier between chunks),
+// so a store that is already close to that order (the particle kernel keeps
+// it between re-sorts) is rewritten in long contiguous runs.  A tile whose
+// rank table exceeds the shared-memory budget keeps its order.
+constexpr int kSortThreads = 256;
+constexpr int kSortMaxCells = 1024;   // tiles up to 32 x 32
+constexpr int kSortMaskWords = 6144;  // ranks x 32-cell words
+constexpr int kSortMaxRank = 2048;
+constexpr int kSortU = 4;             // chunks of slots per memory round trip
+
+size_t sort_smem_bytes() {
+  return (2 * (size_t)kSortMaskWords + kSortMaxRank + 1) * sizeof(unsigned);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSortThreads, 3)
+    sort_tiles_kernel(const SimDev<R> *__restrict__ sims,
+                      int n_sims, const int2 *__restrict__ items,
+                      int n_items, BatchStatus *st) {
+  __shared__ int hist[kSortMaxCells];  // cell counts, then rank cursors
+  __shared__ int wsum[kSortThreads / 32];
+  __shared__ int s_max;
+  extern __shared__ unsigned sort_smem[];
+  unsigned *mask = sort_smem;
+  unsigned *pre = sort_smem + kSortMaskWords;
+  int *T = reinterpret_cast<int *>(sort_smem + 2 * kSortMaskWords);
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kSortThreads / 32;
+  // most steps re-sort nothing: leave at once unless some simulation is due
+  {
+    bool due = false;
+    for (int i = threadIdx.x; i < n_sims && !due; i += blockDim.x)
+      due = sort_due(sims[i], step);
+    if (!__syncthreads_or(due)) return;
+  }
+  for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+    const int2 it = items[ii];
+    const SimDev<R> &S = sims[it.x];
+    if (!sort_due(S, step)) continue;
+    const int tile = it.y;
+    const int tcx = tile % S.ntx, tcy = tile / S.ntx;
+    const int tw = min(S.tx, S.nx - tcx * S.tx);
+    const int th = min(S.ty, S.ny - tcy * S.ty);
+    const int nc = tw * th;
+    const int W = (nc + 31) >> 5;
+    // the copy the push and the migration of this step wrote
+    const int src = ((step + 1) & 1) ^ *S.pswap;
+    for (int s = 0; s < S.nsp; ++s) {
+      const SpeciesDev<R> &P = S.sp[s];
+      const Planes<R> &I = P.buf[src];
+      const Planes<R> &O = P.buf[src ^ 1];
+      const int n = P.cnt[tile];
+      const size_t base = (size_t)P.off[tile];
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) hist[c] = 0;
+      if (threadIdx.x == 0) s_max = 0;
+      __syncthreads();
+#pragma unroll 4
+      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int lc = I.cell[base + p];
+        atomicAdd(&hist[(lc >> 8) * tw + (lc & 255)], 1);
+      }
+      __syncthreads();
+      int m = 0;
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) m = max(m, hist[c]);
+      for (int o = 16; o > 0; o >>= 1)
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(&s_max, m);
+      __syncthreads();
+      const int maxc = s_max;
+      const bool fits = maxc <= kSortMaxRank &&
+                        (long long)maxc * W <= kSortMaskWords;
+      if (fits) {
+        // bit masks: word (r, j) has bit i set when cell 32 j + i holds
+        // more than r particles
+        for (int q = warp; q < maxc * W; q += NW) {
+          const int r = q / W, c = (q - r * W) * 32 + lane;
+          const unsigned b =
+              __ballot_sync(0xffffffffu, c < nc && hist[c] > r);
+          if (lane == 0) mask[q] = b;
+        }
+        __syncthreads();
+        // prefix counts of the words of each rank (one warp per rank,
+        // W <= 32 words), and N(r) = the cells with more than r particles
+        for (int r = warp; r < maxc; r += NW) {
+          const int v = lane < W ? __popc(mask[r * W + lane]) : 0;
+          int x = v;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+          }
+          if (lane < W) pre[r * W + lane] = (unsigned)(x - v);
+          if (lane == 31) T[r] = x;
+        }
+        __syncthreads();
+        // T(r) = particles of rank below r: exclusive scan of N over r
+        int carry = 0;
+        for (int r0 = 0; r0 < maxc; r0 += kSortThreads) {
+          const int r = r0 + threadIdx.x;
+          const int v = r < maxc ? T[r] : 0;
+          int total;
+          const int e = block_exclusive_scan<kSortThreads>(v, wsum, total);
+          if (r < maxc) T[r] = carry + e;
+          carry += total;
+        }
+      }
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) hist[c] = 0;
+      __syncthreads();
+      // kSortU chunks of slots per round trip: every thread loads its
+      // particle of each chunk first, then the chunks take their ranks one
+      // after the other
+      constexpr int U = sizeof(R) == 4 ? kSortU : 2;
+      for (int p0 = 0; p0 < n; p0 += U * kSortThreads) {
+        int lc[U];
+        R x[U], y[U], ux[U], uy[U], uz[U], w[U];
+        int id[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int p = p0 + k * kSortThreads + threadIdx.x;
+          if (p < n) {
+            const size_t q = base + p;
+            lc[k] = I.cell[q];
+            x[k] = I.x[q];
+            y[k] = I.y[q];
+            ux[k] = I.ux[q];
+            uy[k] = I.uy[q];
+            uz[k] = I.uz[q];
+            w[k] = I.w ? I.w[q] : R(1);
+            id[k] = I.id ? I.id[q] : 0;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int p = p0 + k * kSortThreads + threadIdx.x;
+          if (p < n) {
+            int d = p;
+            if (fits) {
+              const int li = (lc[k] >> 8) * tw + (lc[k] & 255);
+              const int r = atomicAdd(&hist[li], 1);
+              const int wd = r * W + (li >> 5);
+              d = T[r] + (int)pre[wd] +
+                  __popc(mask[wd] & ((1u << (li & 31)) - 1u));
+            }
+            const size_t t = base + d;
+            O.cell[t] = (uint16_t)lc[k];
+            O.x[t] = x[k];
+            O.y[t] = y[k];
+            O.ux[t] = ux[k];
+            O.uy[t] = uy[k];
+            O.uz[t] = uz[k];
+            if (I.w) O.w[t] = w[k];
+            if (I.id) O.id[t] = id[k];
+          }
+          __syncthreads();  // this chunk's ranks before the next chunk's
+        }
+      }
+    }
+  }
+}
+
+template <typename R>
+cudaError_t prepare_sort_tiles() {
+  return cudaFuncSetAttribute(sort_tiles_kernel<R>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sort_smem_bytes());
+}
+
+template <typename R>
+cudaError_t launch_sort_tiles(const SimDev<R> *sims, int n_sims,
+                              const int2 *items, int n_items, BatchStatus *st,
+                              cudaStream_t stream) {
+  if (n_items == 0) return cudaSuccess;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+          cudaSuccess)
+    sms = 148;
+  const int grid = n_items < 3 * sms ? n_items : 3 * sms;
+  sort_tiles_kernel<R><<<grid, kSortThreads, sort_smem_bytes(), stream>>>(
+      sims, n_sims, items, n_items, st);
+  return cudaGetLastError();
+}
+
+template cudaError_t prepare_sort_tiles<float>();
+template cudaError_t prepare_sort_tiles<double>();
+template cudaError_t launch_sort_tiles<float>(const SimDev<float> *, int,
+                                              const int2 *, int,
+                                              BatchStatus *, cudaStream_t);
+template cudaError_t launch_sort_tiles<double>(const SimDev<double> *, int,
+                                               const int2 *, int,
+                                               BatchStatus *, cudaStream_t);
 
 // ---- binning ---------------------------------------------------------------
 

@@ -537,6 +537,7 @@ struct TileCtx {
   unsigned char *stages;  // particle-copy ring
   int x0, y0, tw, th, nx, ny;
   int tile, sim, step, shift;
+  int pc;  // current copy of the particle store
   R dt_dx, dt_dy;
   bool do_energy;
   int *s_slots;
@@ -555,8 +556,8 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const SpeciesDev<R> &P = S.sp[s];
-  const Planes<R> &I = P.buf[CUR];
-  const Planes<R> &O = P.buf[CUR ^ 1];
+  const Planes<R> &I = P.buf[T.pc];
+  const Planes<R> &O = P.buf[T.pc ^ 1];
   const bool has_w = kSpec ? !kPlain : I.w != nullptr;
   const bool has_id = kSpec ? !kPlain : I.id != nullptr;
   const bool open_x = kSpec ? kOpen : S.open_x != 0;
@@ -837,6 +838,7 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
   T.tile = tile;
   T.sim = sim;
   T.step = step;
+  T.pc = CUR ^ *S.pswap;
   T.dt_dx = S.dt_dx;
   T.dt_dy = S.dt_dy;
   T.s_slots = s_slots;
@@ -889,7 +891,7 @@ __device__ __forceinline__ void push_tile(const SimDev<R> &S, const int sim,
   unsigned g = 0;  // chunks this warp has taken through the particle ring
   for (int s = 0; s < nsp; ++s) {
     if constexpr (kSpec) {
-      const Planes<R> &I = S.sp[s].buf[CUR];
+      const Planes<R> &I = S.sp[s].buf[T.pc];
       const bool plain = I.w == nullptr && I.id == nullptr;
       if (plain && open_x)
         push_species<R, CUR, true, true, true>(S, s, T, g, st, ovf);
@@ -998,8 +1000,11 @@ cudaError_t prepare_push_deposit(int max_tx, int max_ty, bool wide) {
 
 // Resident CTAs of kernel k per SM for `smem` bytes of dynamic shared
 // memory, times the SM count: the grid of the persistent push kernel.
+// ctas_per_sm > 0 caps the resident CTAs per SM (the tiles in flight per
+// SM, which the autotuner chooses); 0 takes all that fit.
 template <typename K>
-static int persistent_grid(K kernel, size_t smem, int n_items) {
+static int persistent_grid(K kernel, size_t smem, int n_items,
+                           int ctas_per_sm) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -1008,14 +1013,30 @@ static int persistent_grid(K kernel, size_t smem, int n_items) {
                                                     smem) != cudaSuccess ||
       per_sm < 1)
     return n_items;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   return n_items < sms * per_sm ? n_items : sms * per_sm;
 }
+
+template <typename R>
+int push_ctas_fit(int tx, int ty, bool wide) {
+  int per_sm = 0;
+  const size_t smem = push_smem_bytes<R>(tx, ty, wide);
+  if (prepare_push_deposit<R>(tx, ty, wide) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, push_deposit_kernel<R, false, 0, 0>, kPT, smem) !=
+      cudaSuccess)
+    return 0;
+  return per_sm;
+}
+template int push_ctas_fit<float>(int, int, bool);
+template int push_ctas_fit<double>(int, int, bool);
 
 template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
                                 int max_ty, bool all16, bool wide,
-                                BatchStatus *st, const OverflowDev<R> &ovf,
+                                int ctas_per_sm, BatchStatus *st,
+                                const OverflowDev<R> &ovf,
                                 cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
   const size_t smem = push_smem_bytes<R>(max_tx, max_ty, wide);
@@ -1025,21 +1046,21 @@ cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
   if (single) {
     if (t16) {
       auto k = push_deposit_kernel<R, false, 16, 16>;
-      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+      k<<<persistent_grid(k, smem, n_items, ctas_per_sm), kPT, smem, stream>>>(
           sims, *single, items, n_items, st, ovf);
     } else {
       auto k = push_deposit_kernel<R, false, 0, 0>;
-      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+      k<<<persistent_grid(k, smem, n_items, ctas_per_sm), kPT, smem, stream>>>(
           sims, *single, items, n_items, st, ovf);
     }
   } else {
     if (t16) {
       auto k = push_deposit_kernel<R, true, 16, 16>;
-      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+      k<<<persistent_grid(k, smem, n_items, ctas_per_sm), kPT, smem, stream>>>(
           sims, SimDev<R>{}, items, n_items, st, ovf);
     } else {
       auto k = push_deposit_kernel<R, true, 0, 0>;
-      k<<<persistent_grid(k, smem, n_items), kPT, smem, stream>>>(
+      k<<<persistent_grid(k, smem, n_items, ctas_per_sm), kPT, smem, stream>>>(
           sims, SimDev<R>{}, items, n_items, st, ovf);
     }
   }
@@ -1053,13 +1074,14 @@ template cudaError_t prepare_push_deposit<double>(int, int, bool);
 template cudaError_t launch_push_deposit<float>(const SimDev<float> *,
                                                 const SimDev<float> *,
                                                 const int2 *, int, int, int,
-                                                bool, bool, BatchStatus *,
+                                                bool, bool, int, BatchStatus *,
                                                 const OverflowDev<float> &,
                                                 cudaStream_t);
 template cudaError_t launch_push_deposit<double>(const SimDev<double> *,
                                                  const SimDev<double> *,
                                                  const int2 *, int, int, int,
-                                                 bool, bool, BatchStatus *,
+                                                 bool, bool, int,
+                                                 BatchStatus *,
                                                  const OverflowDev<double> &,
                                                  cudaStream_t);
 

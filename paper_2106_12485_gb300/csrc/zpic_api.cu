@@ -44,6 +44,7 @@ namespace zp {
 // error reporting for the ABI entry points defined in other files
 int set_last_error(int code, const char *msg) { return fail(code, msg); }
 bool tuned_tile(const zpic_config &c, int *tx, int *ty);  // autotune.cu
+bool tuned_setting(const zpic_config &c, zpic_tuning *t);  // autotune.cu
 }  // namespace zp
 
 static int cuda_fail(cudaError_t e, const char *what) {
@@ -156,6 +157,10 @@ int validate(const zpic_config *c) {
     return fail(ZPIC_EINVAL, "capacity_slack out of range");
   if (c->flags & ~(ZPIC_TRACK_IDS | ZPIC_FILTER_J))
     return fail(ZPIC_EINVAL, "unknown flags");
+  if (c->sort_every < -1)
+    return fail(ZPIC_EINVAL, "sort_every must be -1, 0 or positive");
+  if (c->push_ctas_per_sm < 0 || c->push_ctas_per_sm > 8)
+    return fail(ZPIC_EINVAL, "push_ctas_per_sm must be in [0, 8]");
   const double dx = c->box_x / c->nx, dy = c->box_y / c->ny;
   const double cfl = 1.0 / std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy));
   if (!(c->dt < cfl)) return fail(ZPIC_ECFL, "dt violates the Courant limit");
@@ -279,6 +284,8 @@ template <typename R>
 struct SimHost {
   zpic_config cfg{};
   int nx, ny, ld, tx, ty, ntx, nty, ntiles, ybx, yby;
+  int sort_every = -1;     // re-sort interval (-1: never)
+  int ctas = 0;            // resident push CTAs per SM (0: all that fit)
   double dx, dy, dt;
   DevMem fields;           // 18 planes of ny * ld
   DevMem part_kin, part_fld, epart, hist, small, energy_rows;
@@ -505,6 +512,8 @@ class Batch : public BatchBase {
     if (t0 < 0 || t0 > t1 || t1 > S.ntiles)
       return fail(ZPIC_EINVAL, "tile range");
     ZP_TRY(read_counts(si, s));
+    int pc = 0;
+    ZP_TRY(particle_copy(si, &pc));
     SpeciesHost<R> &P = S.sp[s];
     std::vector<long long> off(std::max(1, t1 - t0));
     long long n = 0;
@@ -535,7 +544,7 @@ class Batch : public BatchBase {
         const int a = t0 + (int)((long long)nt * c / kChunks);
         const int b = t0 + (int)((long long)nt * (c + 1) / kChunks);
         if (a == b) continue;
-        ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty,
+        ZP_CU(launch_compact<R>(S.dev.sp[s], pc, S.tx, S.ty,
                                 S.ntx, a, b - a,
                                 (const long long *)stg_off_.p + (a - t0),
                                 stg_, stream_));
@@ -555,7 +564,7 @@ class Batch : public BatchBase {
       ZP_CU(cudaStreamSynchronize(stream_));
       return ZPIC_OK;
     }
-    ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty, S.ntx,
+    ZP_CU(launch_compact<R>(S.dev.sp[s], pc, S.tx, S.ty, S.ntx,
                             t0, t1 - t0, (const long long *)stg_off_.p, stg_,
                             stream_));
     ZP_CU(cudaMemcpyAsync(d->ix, stg_.ix, 4 * n, cudaMemcpyDeviceToHost, stream_));
@@ -725,6 +734,10 @@ class Batch : public BatchBase {
     }
     o->resorts = resorts_;
     o->device_bytes = bytes_;
+    o->sort_every = S.sort_every;
+    o->push_ctas_per_sm = resolved_ctas();
+    ZP_CU(cudaMemcpy(&o->sorts, S.dev.sorts, sizeof(int),
+                     cudaMemcpyDeviceToHost));
     ZP_CU(cudaMemcpy(o->push_variants, S.dev.variants,
                      sizeof(int) * kMaxSpecies, cudaMemcpyDeviceToHost));
     return ZPIC_OK;
@@ -816,9 +829,14 @@ class Batch : public BatchBase {
     ps.scale[0] = (double)nbx / (range[1] - range[0]);
     ps.scale[1] = (double)nby / (range[3] - range[2]);
     ps.q0 = std::fabs(S.sp[s].q0);
+    int pc = 0;
+    if (particle_copy(si, &pc) != ZPIC_OK) {
+      dfree(h);
+      return ZPIC_ECUDA;
+    }
     cudaError_t e = cudaMemsetAsync(h.p, 0, bytes, stream_);
     if (e == cudaSuccess)
-      e = launch_phasespace<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty, S.ntx,
+      e = launch_phasespace<R>(S.dev.sp[s], pc, S.tx, S.ty, S.ntx,
                                S.ntiles, ps, (double *)h.p, stream_);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst, h.p, bytes, cudaMemcpyDeviceToHost, stream_);
@@ -979,7 +997,7 @@ class Batch : public BatchBase {
     D.hist_skip = 0;
     if (!dalloc(S.energy_rows, sizeof(double) * (2 * (size_t)S.ny + 2)))
       return fail(ZPIC_ENOMEM, "energy scratch");
-    if (!dalloc(S.small, sizeof(int) * (3 + 3 * kMaxSpecies)))
+    if (!dalloc(S.small, sizeof(int) * (5 + 3 * kMaxSpecies)))
       return fail(ZPIC_ENOMEM, "counters");
     ZP_CU(cudaMemsetAsync(S.small.p, 0, S.small.bytes, stream_));
     D.hist_n = (int *)S.small.p;
@@ -988,6 +1006,20 @@ class Batch : public BatchBase {
     D.ob_need = (int *)S.small.p + 2 + kMaxSpecies;
     D.eticket = (int *)S.small.p + 2 + 2 * kMaxSpecies;
     D.variants = (int *)S.small.p + 3 + 2 * kMaxSpecies;
+    D.pswap = (int *)S.small.p + 3 + 3 * kMaxSpecies;
+    D.sorts = (int *)S.small.p + 4 + 3 * kMaxSpecies;
+    // cell-order re-sort interval and resident push CTAs: the configured
+    // values, else those the autotuner chose for the class, else never / all
+    // that fit
+    {
+      zpic_tuning t{};
+      const bool tuned = tuned_setting(c, &t);
+      S.sort_every = c.sort_every > 0 ? c.sort_every
+                     : (c.sort_every == 0 && tuned ? t.sort_every : -1);
+      S.ctas = c.push_ctas_per_sm > 0 ? c.push_ctas_per_sm
+               : (tuned ? t.push_ctas_per_sm : 0);
+      D.sort_every = S.sort_every > 0 ? S.sort_every : 0;
+    }
 
     // species: initial per-tile counts from the profile, then capacities
     S.sp.resize(c.n_species);
@@ -1422,7 +1454,9 @@ class Batch : public BatchBase {
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
     if (ready) ZP_CU(cudaStreamWaitEvent(stream_, ready, 0));
-    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], h_st_->step & 1, S.tx,
+    int pc = 0;
+    ZP_TRY(particle_copy(si, &pc));
+    ZP_CU(launch_bin_scatter<R>(stg_, n, S.dev.sp[s], pc, S.tx,
                                 S.ty, has_w ? 1 : 0, has_id ? 1 : 0, stream_));
     P.h_cnt = cnt;
     ZP_TRY(upload_descriptors());
@@ -1492,7 +1526,9 @@ class Batch : public BatchBase {
         ZP_TRY(ensure_staging(n + extra + 1));
         ZP_CU(cudaMemcpyAsync(stg_off_.p, off.data(), sizeof(long long) * S.ntiles,
                               cudaMemcpyHostToDevice, stream_));
-        ZP_CU(launch_compact<R>(S.dev.sp[s], h_st_->step & 1, S.tx, S.ty,
+        int pc = 0;
+        ZP_TRY(particle_copy(si, &pc));
+        ZP_CU(launch_compact<R>(S.dev.sp[s], pc, S.tx, S.ty,
                                 S.ntx, 0, S.ntiles,
                                 (const long long *)stg_off_.p, stg_, stream_));
         ZP_CU(cudaMemsetAsync(bad_.p, 0, 4, stream_));
@@ -1510,6 +1546,24 @@ class Batch : public BatchBase {
     return ZPIC_OK;
   }
 
+  // The current copy of simulation si's particle store, (step & 1) ^ pswap
+  // (the device flips pswap after a cell-order re-sort); after a sync.
+  int particle_copy(int si, int *pc) {
+    int p = 0;
+    ZP_CU(cudaMemcpy(&p, sims_[si].dev.pswap, sizeof(int),
+                     cudaMemcpyDeviceToHost));
+    *pc = (h_st_->step & 1) ^ (p & 1);
+    return ZPIC_OK;
+  }
+
+  // Resident push CTAs per SM of the batch: its first member's setting
+  // (0: all that fit), reported as the number in use.
+  int resolved_ctas() const {
+    const SimHost<R> &S = sims_[0];
+    const int fit = push_ctas_fit<R>(max_tx_, max_ty_, ring_wide());
+    return S.ctas > 0 && S.ctas < fit ? S.ctas : fit;
+  }
+
   // ---- launch sequence ---------------------------------------------------------
 
   const SimDev<R> *dsims() const { return (const SimDev<R> *)sims_dev_.p; }
@@ -1525,10 +1579,18 @@ class Batch : public BatchBase {
   // the kernels of one step, in order (the filter only when some
   // simulation of the batch filters its current)
   std::vector<int> stages() const {
-    bool filter = false;
-    for (const auto &S : sims_) filter = filter || S.dev.Jf[0] != nullptr;
-    if (filter) return {0, 4, 1, 2, 3};
-    return {0, 1, 2, 3};
+    bool filter = false, sort = false;
+    for (const auto &S : sims_) {
+      filter = filter || S.dev.Jf[0] != nullptr;
+      sort = sort || S.dev.sort_every > 0;
+    }
+    std::vector<int> k = {0};
+    if (filter) k.push_back(4);
+    k.push_back(1);
+    k.push_back(2);
+    if (sort) k.push_back(5);
+    k.push_back(3);
+    return k;
   }
 
   cudaError_t launch_stage(int k) {
@@ -1538,8 +1600,7 @@ class Batch : public BatchBase {
         return launch_push_deposit<R>(dsims(), n_sims == 1 ? &sims_[0].dev : nullptr,
                                       (const int2 *)items_.p, n_items_,
                                       max_tx_, max_ty_, all16_, ring_wide(),
-                                      dst(), ovf_,
-                                      stream_);
+                                      sims_[0].ctas, dst(), ovf_, stream_);
       case 1:
         return launch_yee<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
                              dst(), stream_);
@@ -1548,14 +1609,18 @@ class Batch : public BatchBase {
                                  dst(), ovf_, stream_);
       case 3:
         return launch_end_step<R>(dsims(), n_sims, dst(), stream_);
+      case 5:
+        return launch_sort_tiles<R>(dsims(), n_sims, (const int2 *)items_.p,
+                                    n_items_, dst(), stream_);
       default:
         return launch_filter<R>(dsims(), (const int2 *)yee_items_.p, n_yee_,
                                 dst(), stream_);
     }
   }
   static const char *stage_name(int k) {
-    static const char *names[5] = {"push_deposit", "yee", "migrate",
-                                   "end_step", "filter_current"};
+    static const char *names[6] = {"push_deposit", "yee", "migrate",
+                                   "end_step", "filter_current",
+                                   "sort_tiles"};
     return names[k];
   }
 
@@ -1563,6 +1628,7 @@ class Batch : public BatchBase {
     if (n == 0) return ZPIC_OK;
     if (profiling_) {
       ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_, ring_wide()));
+      ZP_CU(prepare_sort_tiles<R>());
       const std::vector<int> order = stages();
       if (timers_.size() != order.size()) {
         timers_.clear();
@@ -1594,6 +1660,7 @@ class Batch : public BatchBase {
     NvtxRange r_("zpic graph capture");
     // kernel attributes are set outside the capture
     ZP_CU(prepare_push_deposit<R>(max_tx_, max_ty_, ring_wide()));
+    ZP_CU(prepare_sort_tiles<R>());
     cudaStream_t cs;
     ZP_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t keep = stream_;

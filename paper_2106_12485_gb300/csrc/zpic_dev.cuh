@@ -14,7 +14,8 @@
 //   particles, per species: SoA arrays cell (uint16, cell within the tile),
 //           x, y, ux, uy, uz (R), optional w (R) and id (int32), one segment per
 //           tile [off[t], off[t] + cap[t]) of which cnt[t] are live; two
-//           copies (read one, write the other each step);
+//           copies (read one, write the other each step; which one is
+//           current is (step & 1) ^ *pswap);
 //   outbox, per species: ob_cap slots per tile for particles that leave it.
 #pragma once
 
@@ -80,7 +81,7 @@ struct SpeciesDev {
                  // FP64: q0 dx/dt, q0 dy/dt, q0 (physical units)
   double kin_scale;  // (q0 / (q/m)) dx dy : mass x cell area, weight 1
   // two copies of the store with one segment layout: the push of step n
-  // reads buf[n & 1] and writes buf[(n + 1) & 1]
+  // reads buf[(n & 1) ^ pswap] and writes the other one
   Planes<R> buf[2];
   int *off, *cap, *cnt;            // per tile
   int ob_cap;                      // outbox slots per tile
@@ -133,6 +134,13 @@ struct SimDev {
                                // (0: none); the re-sort grows the outbox
   int *variants;               // [kMaxSpecies] bits of the push-kernel forms
                                // that ran for the species (ZPIC_PUSH_*)
+  // Which copy of the particle store is current: copy (step & 1) ^ *pswap.
+  // The re-sort after step n (when due) writes the other copy in cell-
+  // interleaved order and the end-of-step kernel flips *pswap, so the next
+  // push reads the sorted copy.  *sorts counts the re-sorts.
+  int *pswap;
+  int *sorts;
+  int sort_every;              // re-sort interval in steps; <= 0: never
   SpeciesDev<R> sp[kMaxSpecies];
 };
 
@@ -159,6 +167,13 @@ __device__ __forceinline__ bool shift_due(const SimDev<R> &S, int step,
                                           int n_shift) {
   return S.moving_window &&
          ((double)(step + 1) * S.dt_d >= (double)(n_shift + 1) * S.dx_d);
+}
+
+// The particle re-sort runs after step `step` (before the step counter
+// advances) every sort_every steps.
+template <typename R>
+__device__ __forceinline__ bool sort_due(const SimDev<R> &S, int step) {
+  return S.sort_every > 0 && ((step + 1) % S.sort_every) == 0;
 }
 
 // Float with the bit pattern b (host and device).

@@ -15,6 +15,10 @@ constexpr int kYeeY = 8;
 template <typename R>
 size_t push_smem_bytes(int tx, int ty, bool wide);
 
+// Resident push-kernel CTAs per SM for tx x ty tiles (0 on failure).
+template <typename R>
+int push_ctas_fit(int tx, int ty, bool wide);
+
 // Sets the push kernel's dynamic shared-memory limit (call before launching
 // or capturing it).
 template <typename R>
@@ -27,7 +31,7 @@ template <typename R>
 cudaError_t launch_push_deposit(const SimDev<R> *sims, const SimDev<R> *single,
                                 const int2 *items, int n_items, int max_tx,
                                 int max_ty, bool all16, bool wide,
-                                BatchStatus *st,
+                                int ctas_per_sm, BatchStatus *st,
                                 const OverflowDev<R> &ovf,
                                 cudaStream_t stream);
 
@@ -49,6 +53,16 @@ template <typename R>
 cudaError_t launch_migrate(const SimDev<R> *sims, const int2 *items,
                            int n_items, BatchStatus *st,
                            const OverflowDev<R> &ovf, cudaStream_t stream);
+
+// Cell-order re-sort of every tile of the simulations that are due after
+// this step (into the other copy of the store; the end-of-step kernel makes
+// it current).  prepare_sort_tiles sets the kernel's shared-memory limit.
+template <typename R>
+cudaError_t prepare_sort_tiles();
+template <typename R>
+cudaError_t launch_sort_tiles(const SimDev<R> *sims, int n_sims,
+                              const int2 *items, int n_items, BatchStatus *st,
+                              cudaStream_t stream);
 
 // Energy records, window counter, step counter.
 template <typename R>

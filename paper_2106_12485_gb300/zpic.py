@@ -53,7 +53,8 @@ class zpic_config(C.Structure):
                 ("laser", zpic_laser), ("seed", C.c_uint64),
                 ("sim_index", C.c_int), ("energy_every", C.c_int),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("flags", C.c_int),
-                ("capacity_slack", C.c_double)]
+                ("capacity_slack", C.c_double), ("sort_every", C.c_int),
+                ("push_ctas_per_sm", C.c_int)]
 
 
 class zpic_particles(C.Structure):
@@ -80,7 +81,15 @@ class zpic_info(C.Structure):
                 ("n_particles", C.c_int64 * MAX_SPECIES),
                 ("capacity", C.c_int64 * MAX_SPECIES),
                 ("resorts", C.c_int32), ("device_bytes", C.c_size_t),
-                ("push_variants", C.c_int32 * MAX_SPECIES)]
+                ("push_variants", C.c_int32 * MAX_SPECIES),
+                ("sort_every", C.c_int32), ("push_ctas_per_sm", C.c_int32),
+                ("sorts", C.c_int32)]
+
+
+class zpic_tuning(C.Structure):
+    _fields_ = [("tile_x", C.c_int), ("tile_y", C.c_int),
+                ("push_ctas_per_sm", C.c_int), ("sort_every", C.c_int),
+                ("ms_per_step", C.c_double)]
 
 
 class zpic_state(C.Structure):
@@ -124,6 +133,9 @@ _PROTOS = {
                                 C.POINTER(C.c_int), C.POINTER(C.c_int), _P,
                                 C.c_int, C.POINTER(C.c_int)]),
     "zpic_autotune_candidates": (C.c_int, [_P, C.c_int]),
+    "zpic_autotune_all": (C.c_int, [C.POINTER(zpic_config), C.c_int,
+                                    C.POINTER(zpic_tuning), _P, C.c_int,
+                                    C.POINTER(C.c_int)]),
     "zpic_profile_enable": (C.c_int, [_P, C.c_int]),
     "zpic_profile_read": (C.c_int, [_P, _P, C.c_size_t, _P, _P, C.c_int,
                                     C.POINTER(C.c_int), C.c_int]),
@@ -199,7 +211,8 @@ def species(q_over_m=-1.0, ppc=(4, 4), u_th=(0.0, 0.0, 0.0),
 def config(nx, ny, box, dt, species_list=(), precision=FP32,
            bc_x=BC_PERIODIC, moving_window=False, laser=None,
            seed=2106012485, sim_index=0, energy_every=0, tile=(0, 0),
-           track_ids=False, capacity_slack=0.0, filter_j=False):
+           track_ids=False, capacity_slack=0.0, filter_j=False,
+           sort_every=0, push_ctas_per_sm=0):
     c = zpic_config()
     c.nx, c.ny = nx, ny
     c.box_x, c.box_y = box
@@ -220,6 +233,8 @@ def config(nx, ny, box, dt, species_list=(), precision=FP32,
     c.tile_x, c.tile_y = tile
     c.flags = (TRACK_IDS if track_ids else 0) | (FILTER_J if filter_j else 0)
     c.capacity_slack = capacity_slack
+    c.sort_every = sort_every
+    c.push_ctas_per_sm = push_ctas_per_sm
     return c
 
 
@@ -439,6 +454,26 @@ def autotune(cfg, steps=10, retune=True):
     times = {(int(xy[2 * k]), int(xy[2 * k + 1])): float(ms[k])
              for k in range(n)} if retune else {}
     return bx.value, by.value, times
+
+
+def autotune_all(cfg, steps=10):
+    """Tile size, resident CTAs per SM and re-sort interval for cfg's class
+    (zpic_autotune_all): (zpic_tuning, list of (stage, candidate, ms per
+    step) in the order they were timed)."""
+    n = lib().zpic_autotune_candidates(None, 0)
+    xy = np.zeros(2 * n, np.int32)
+    lib().zpic_autotune_candidates(_ptr(xy), n)
+    ms = np.zeros(64)
+    t = zpic_tuning()
+    nc = C.c_int()
+    check(lib().zpic_autotune_all(C.byref(cfg), steps, C.byref(t), _ptr(ms),
+                                  ms.size, C.byref(nc)), "zpic_autotune_all")
+    n_cta = nc.value - n - 4
+    labels = ([("tile", (int(xy[2 * k]), int(xy[2 * k + 1])))
+               for k in range(n)] +
+              [("ctas_per_sm", k + 1) for k in range(n_cta)] +
+              [("sort_every", v) for v in (-1, 10, 20, 40)])
+    return t, [(a, b, float(ms[k])) for k, (a, b) in enumerate(labels)]
 
 
 def load_checkpoint(cfg, path):
