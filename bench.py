@@ -347,8 +347,18 @@ def fp32_over_fp64(args, stream, torch, fp32_value, steps=5):
     drift = max(abs(t - tot[0]) for t in tot) / tot[0]
     del sim
     v64 = n * steps / (ms / 1e3)
+    # the same with the fixed-point (bitwise reproducible) FP64 current
+    cfg_d = W.precision_study(args.nx, args.ny, ppc=(args.ppc, args.ppc),
+                              precision=Z.FP64, deterministic=True)
+    sim = Z.Sim(cfg_d)
+    sim.set_stream(stream.cuda_stream)
+    sim.step(2)
+    sim.sync()
+    ms_d = timed_steps(sim, stream, steps, torch)
+    del sim
     return {"fp64_value": v64, "fp64_ms_per_step": ms / steps,
             "fp64_steps": steps, "fp64_energy_drift": drift,
+            "fp64_deterministic_value": n * steps / (ms_d / 1e3),
             "ratio": fp32_value / v64}
 
 

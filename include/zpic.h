@@ -106,6 +106,19 @@ extern "C" {
                                   axis one (1,2,1)/4 and one (-1,6,-1)/4
                                   pass; the J getters then return the
                                   filtered current */
+#define ZPIC_DETERMINISTIC 4   /* bitwise reproducible runs: the current of
+                                  a step is an exact integer sum, whatever
+                                  order tiles and particles add in, so
+                                  fields, currents, particles and field
+                                  energies repeat bit for bit (the kinetic
+                                  energy records sum per-particle values
+                                  in store order and repeat to rounding).
+                                  FP32 always works this way (this flag
+                                  changes nothing); FP64 then sums J as
+                                  64-bit fixed point in units of 2^-47 of
+                                  the largest one-segment contribution
+                                  (range 2^16 such units per value and
+                                  step) instead of double atomics */
 
 typedef struct {
     double q_over_m;    /* charge-to-mass ratio (electrons: -1)          */
@@ -146,7 +159,8 @@ typedef struct {
     int tile_x, tile_y;         /* tile size in cells, 2..32; 0: the size
                                    zpic_autotune chose for this
                                    configuration's class, else 16         */
-    int flags;                  /* ZPIC_TRACK_IDS | ZPIC_FILTER_J         */
+    int flags;                  /* ZPIC_TRACK_IDS | ZPIC_FILTER_J |
+                                   ZPIC_DETERMINISTIC                     */
     double capacity_slack;      /* spare tile capacity fraction; 0: 0.25  */
     int sort_every;             /* re-sort every tile's particles into
                                    cell-interleaved order every k steps

@@ -71,6 +71,8 @@ template <typename R>
 __device__ __forceinline__ R j_scale(const SimDev<R> &S, int c, JRaw<R> v) {
   if constexpr (sizeof(R) == 4)
     return fixed_to_float(v) * S.jscale[c];
+  else if (S.jfixed)
+    return (double)__double_as_longlong(v) * S.jscale_d[c];
   else
     return v;
 }

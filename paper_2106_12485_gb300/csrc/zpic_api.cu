@@ -155,7 +155,7 @@ int validate(const zpic_config *c) {
     return fail(ZPIC_EINVAL, "tile sizes must be 0 or in [2, 32]");
   if (c->capacity_slack < 0 || c->capacity_slack > 16)
     return fail(ZPIC_EINVAL, "capacity_slack out of range");
-  if (c->flags & ~(ZPIC_TRACK_IDS | ZPIC_FILTER_J))
+  if (c->flags & ~(ZPIC_TRACK_IDS | ZPIC_FILTER_J | ZPIC_DETERMINISTIC))
     return fail(ZPIC_EINVAL, "unknown flags");
   if (c->sort_every < -1)
     return fail(ZPIC_EINVAL, "sort_every must be -1, 0 or positive");
@@ -423,6 +423,9 @@ class Batch : public BatchBase {
     else if (sizeof(R) == 4)
       return get_current_fixed(S, S.dev.Jq[(step + 1) & 1][which - 6],
                                S.dev.jscale[which - 6], dst, want_f64);
+    else if (S.dev.jfixed)
+      return get_current_fixed64(S, S.dev.J[(step + 1) & 1][which - 6],
+                                 S.dev.jscale_d[which - 6], dst, want_f64);
     else
       src = S.dev.J[(step + 1) & 1][which - 6];  // last step's current
     const bool same = want_f64 == (sizeof(R) == 8);
@@ -464,6 +467,26 @@ class Batch : public BatchBase {
         ((double *)dst)[k] = v;
       else
         ((float *)dst)[k] = v;
+    }
+    return ZPIC_OK;
+  }
+
+  // FP64 with ZPIC_DETERMINISTIC: int64 fixed-point sums in the J words,
+  // scaled as the kernels do ((double) value * scale)
+  int get_current_fixed64(SimHost<R> &S, const R *src, double scale,
+                          void *dst, int want_f64) {
+    const size_t n = (size_t)S.nx * S.ny;
+    std::vector<long long> q(n);
+    ZP_CU(cudaMemcpy2DAsync(q.data(), S.nx * sizeof(long long), src,
+                            S.ld * sizeof(long long), S.nx * sizeof(long long),
+                            S.ny, cudaMemcpyDeviceToHost, stream_));
+    ZP_CU(cudaStreamSynchronize(stream_));
+    for (size_t k = 0; k < n; ++k) {
+      const double v = (double)q[k] * scale;
+      if (want_f64)
+        ((double *)dst)[k] = v;
+      else
+        ((float *)dst)[k] = (float)v;
     }
     return ZPIC_OK;
   }
@@ -955,6 +978,7 @@ class Batch : public BatchBase {
     D.ybx = S.ybx;
     D.yby = S.yby;
     D.open_x = c.bc_x == ZPIC_BC_OPEN;
+    D.jfixed = sizeof(R) == 8 && (c.flags & ZPIC_DETERMINISTIC) ? 1 : 0;
     D.moving_window = c.moving_window ? 1 : 0;
     D.energy_every = c.energy_every;
     D.nsp = c.n_species;
@@ -1089,11 +1113,15 @@ class Batch : public BatchBase {
     if (!(uq > 0)) uq = 1.0;
     const double cx = S.dx / S.dt, cy = S.dy / S.dt;
     const bool fp32 = sizeof(R) == 4;
+    // FP64 fixed point: contributions in units of 2^-47 Uq
+    const double u47 = std::ldexp(1.0, 47);
     for (int s = 0; s < (int)S.sp.size(); ++s) {
       SpeciesDev<R> &Q = S.dev.sp[s];
       const double q0 = S.sp[s].q0;
       if (fp32) {
         Q.dq[0] = Q.dq[1] = Q.dq[2] = (R)(q0 / uq * 65536.0);
+      } else if (S.dev.jfixed) {
+        Q.dq[0] = Q.dq[1] = Q.dq[2] = (R)(q0 / uq * u47);
       } else {
         Q.dq[0] = (R)(q0 * cx);
         Q.dq[1] = (R)(q0 * cy);
@@ -1104,6 +1132,10 @@ class Batch : public BatchBase {
     S.dev.jscale[0] = fp32 ? (float)(uq * cx * u30) : 1.0f;
     S.dev.jscale[1] = fp32 ? (float)(uq * cy * u30) : 1.0f;
     S.dev.jscale[2] = fp32 ? (float)(uq * u30) : 1.0f;
+    const double i47 = std::ldexp(1.0, -47);
+    S.dev.jscale_d[0] = uq * cx * i47;
+    S.dev.jscale_d[1] = uq * cy * i47;
+    S.dev.jscale_d[2] = uq * i47;
   }
 
   // Allocates the tile store of species s for per-tile counts cnt.

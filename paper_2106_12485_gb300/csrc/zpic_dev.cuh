@@ -117,6 +117,10 @@ struct SimDev {
   // contributes at most one unit) and add it to Jq; a sum v reads as
   // J = float(v) * jscale, two FP32 roundings (no FP64 on the field path).
   float jscale[3];
+  // FP64 with ZPIC_DETERMINISTIC: J words hold int64 fixed-point sums
+  // (units 2^-47 of Uq dx/dt, Uq dy/dt, Uq), read as value * jscale_d
+  int jfixed;
+  double jscale_d[3];
   double *part_kin;            // [kMaxSpecies][ntiles] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
   double *epart;               // [kEndSlices][kEndQ][2] compensated sums
@@ -210,6 +214,8 @@ __device__ __forceinline__ R j_value(const SimDev<R> &S, int cur, int c,
                                      size_t idx) {
   if constexpr (sizeof(R) == 4)
     return fixed_to_float(S.Jq[cur][c][idx]) * S.jscale[c];
+  else if (S.jfixed)
+    return (double)__double_as_longlong(S.J[cur][c][idx]) * S.jscale_d[c];
   else
     return S.J[cur][c][idx];
 }

@@ -26,6 +26,7 @@ FIELD_IDS = {"ex": EX, "ey": EY, "ez": EZ, "bx": BX, "by": BY, "bz": BZ,
 PROFILE_NONE, PROFILE_UNIFORM, PROFILE_SLAB, PROFILE_RAMP = 0, 1, 2, 3
 TRACK_IDS = 1
 FILTER_J = 2
+DETERMINISTIC = 4
 PUSH_GENERIC, PUSH_PLAIN_PERIODIC, PUSH_PLAIN_OPEN = 1, 2, 4
 
 
@@ -212,7 +213,7 @@ def config(nx, ny, box, dt, species_list=(), precision=FP32,
            bc_x=BC_PERIODIC, moving_window=False, laser=None,
            seed=2106012485, sim_index=0, energy_every=0, tile=(0, 0),
            track_ids=False, capacity_slack=0.0, filter_j=False,
-           sort_every=0, push_ctas_per_sm=0):
+           sort_every=0, push_ctas_per_sm=0, deterministic=False):
     c = zpic_config()
     c.nx, c.ny = nx, ny
     c.box_x, c.box_y = box
@@ -231,7 +232,8 @@ def config(nx, ny, box, dt, species_list=(), precision=FP32,
     c.sim_index = sim_index
     c.energy_every = energy_every
     c.tile_x, c.tile_y = tile
-    c.flags = (TRACK_IDS if track_ids else 0) | (FILTER_J if filter_j else 0)
+    c.flags = ((TRACK_IDS if track_ids else 0) | (FILTER_J if filter_j else 0)
+               | (DETERMINISTIC if deterministic else 0))
     c.capacity_slack = capacity_slack
     c.sort_every = sort_every
     c.push_ctas_per_sm = push_ctas_per_sm
