@@ -638,19 +638,27 @@ def other_workload(args):
             kernels_ms_next_steps=stage_split(sim, args.steps))))
         return
     if args.workload == "tiles":
-        # the autotuner's tile-size sweep for the workload classes (each on
-        # its copy reduced to at most 1024 x 1024 cells)
+        # the autotuner for the workload classes (each on its copy reduced
+        # to at most 1024 x 1024 cells): tile size, then resident push CTAs
+        # per SM, then the cell-order re-sort interval
         out = {}
         for name, cfg in (("uniform_2048", W.precision_study()),
                           ("clouds_1024", W.clouds()),
                           ("lwfa_4096x512", W.lwfa()),
                           ("weibel_512", W.weibel())):
-            bx, by, times = Z.autotune(cfg, steps=args.steps)
-            out[name] = {"best": [bx, by],
-                         "ms_per_step": {"%dx%d" % k: round(v, 4)
-                                         for k, v in times.items()}}
-        print(json.dumps({"workload": "tile-size sweep (autotuner)",
-                          "steps": args.steps, "classes": out}))
+            t, times = Z.autotune_all(cfg, steps=args.steps)
+            stages = {}
+            for stage, cand, ms in times:
+                key = "%dx%d" % cand if stage == "tile" else str(cand)
+                stages.setdefault(stage, {})[key] = round(ms, 4)
+            out[name] = {"best": {"tile": [t.tile_x, t.tile_y],
+                                  "ctas_per_sm": t.push_ctas_per_sm,
+                                  "sort_every": t.sort_every,
+                                  "ms_per_step": round(t.ms_per_step, 4)},
+                         "ms_per_step": stages}
+        print(json.dumps({"workload": "autotuner: tile size, CTAs per SM, "
+                          "re-sort interval", "steps": args.steps,
+                          "classes": out}))
         return
     if args.workload == "precision":
         # FP32 vs FP64 at equal energy-conservation error: for each form the

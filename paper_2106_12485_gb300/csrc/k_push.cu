@@ -396,10 +396,17 @@ __device__ __forceinline__ RingLane ring_lane(const Planes<R> &I, int lane) {
   return r;
 }
 
-__device__ __forceinline__ void ring_issue(const RingLane &r, unsigned stg,
-                                           int p0) {
-  if (r.n > 0) cp_async16(stg + r.dst[0], r.src[0] + ((size_t)p0 << r.sh[0]));
-  if (r.n > 1) cp_async16(stg + r.dst[1], r.src[1] + ((size_t)p0 << r.sh[1]));
+// A warp takes consecutive chunks: its lanes' sources start at the warp's
+// first particle (ring_start) and advance by one chunk per copy.
+__device__ __forceinline__ void ring_start(RingLane &r, int p0) {
+  r.src[0] += (size_t)p0 << r.sh[0];
+  r.src[1] += (size_t)p0 << r.sh[1];
+}
+__device__ __forceinline__ void ring_issue_next(RingLane &r, unsigned stg) {
+  if (r.n > 0) cp_async16(stg + r.dst[0], r.src[0]);
+  if (r.n > 1) cp_async16(stg + r.dst[1], r.src[1]);
+  r.src[0] += 32u << r.sh[0];
+  r.src[1] += 32u << r.sh[1];
 }
 
 template <typename R>
@@ -628,11 +635,10 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   RingLane rl;
   if constexpr (kS > 0) {
     rl = ring_lane(I, lane);
+    ring_start(rl, base + r0);
     // prologue: chunks 0 .. kS-2 (one commit group each, empty or not)
     for (int jc = 0; jc < kS - 1; ++jc) {
-      if (jc < nch)
-        ring_issue(rl, stg0 + ((g + jc) % kS) * sbytes,
-                   base + r0 + jc * 32);
+      if (jc < nch) ring_issue_next(rl, stg0 + ((g + jc) % kS) * sbytes);
       cp_async_commit();
     }
   }
@@ -649,8 +655,7 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
       // the stage of chunk jc + kS - 1 was read in the previous iteration
       __syncwarp();
       if (jc + kS - 1 < nch)
-        ring_issue(rl, stg0 + ((g + kS - 1) % kS) * sbytes,
-                   c0 + base + (kS - 1) * 32);
+        ring_issue_next(rl, stg0 + ((g + kS - 1) % kS) * sbytes);
       cp_async_commit();
       cp_async_wait<kS - 1>();  // this lane's pieces of chunk jc landed
       __syncwarp();             // ... and every other lane's
@@ -681,11 +686,15 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
     }
     const R wd = valid ? w : R(0);
     int lx = lc & 255, ly = lc >> 8;
-    if (lx >= tw || ly >= th) {
-      // never produced by the library's own kernels: record it and keep
-      // the shared-memory accesses inside the tile
-      atomicOr(&st->error, ERR_STORE);
-      atomicMin(&st->err_step, T.step);
+    // never produced by the library's own kernels: record it and keep
+    // the shared-memory accesses inside the tile (a warp-uniform test,
+    // then the rare lanes)
+    const bool bad = lx >= tw || ly >= th;
+    if (__any_sync(0xffffffffu, bad)) {
+      if (bad) {
+        atomicOr(&st->error, ERR_STORE);
+        atomicMin(&st->err_step, T.step);
+      }
       lx = min(lx, tw - 1);
       ly = min(ly, th - 1);
     }
@@ -754,16 +763,27 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
     }
 
     // ---- new cell: window shift, boundaries, tile membership ----
-    int nix = T.x0 + lx + ps.di - T.shift;
-    const int niy = wrap1(T.y0 + ly + ps.dj, T.ny);
-    bool removed = false;
+    int nix, niy, nlx, nly;
+    bool removed = false, inside;
+    // in the tile's own coordinates first; the global cell, the
+    // boundaries and the periodic wrap only for particles that leave the
+    // tile's cells (a wrap may bring one back into a tile that spans the
+    // box)
+    nlx = lx + ps.di - T.shift;
+    nly = ly + ps.dj;
+    nix = T.x0 + nlx;
+    niy = T.y0 + nly;
     if (open_x)  // leaves the window it moved in, or the shifted window
       removed = nix + T.shift >= T.nx || nix < 0;
-    else
-      nix = wrap1(nix, T.nx);
-    const int nlx = nix - T.x0, nly = niy - T.y0;
-    const bool inside =
-        (unsigned)nlx < (unsigned)tw && (unsigned)nly < (unsigned)th;
+    inside = !removed && (unsigned)nlx < (unsigned)tw &&
+             (unsigned)nly < (unsigned)th;
+    if (!inside && !removed) {
+      niy = wrap1(niy, T.ny);
+      if (!open_x) nix = wrap1(nix, T.nx);
+      nlx = nix - T.x0;
+      nly = niy - T.y0;
+      inside = (unsigned)nlx < (unsigned)tw && (unsigned)nly < (unsigned)th;
+    }
     const bool stay = valid && !removed && inside;
     const bool leave = valid && !removed && !inside;
     if (valid && removed) ++n_removed;
