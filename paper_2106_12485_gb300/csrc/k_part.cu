@@ -5,6 +5,8 @@
 // by the overflow re-sort.
 #include <math.h>
 
+#include <algorithm>
+
 #include "zpic_dev.cuh"
 #include "zpic_kernels.h"
 
@@ -12,18 +14,20 @@ namespace zp {
 
 // ---- migration --------------------------------------------------------------
 //
-// One CTA per tile: scans the outboxes of its distinct neighbour tiles, keeps
-// the entries whose cell lies in this tile and appends them behind the tile's
-// stayers.  The neighbours' outboxes are read as one concatenated list in
-// passes of kMigE entries per thread: all entries of a pass are loaded
-// first, a block-wide prefix sum of the kept entries gives their slots and
-// lists them in shared memory in slot order, then each thread copies one
-// listed entry, so a tile waits for a few memory round trips instead of one
-// per neighbour, every lane of a warp copies, and the order of the arrivals
-// is fixed.  Tiles in the
-// last column also receive the new plasma column when the window shifts.
-// Particles that find no room go to the overflow buffer and raise
-// ERR_OVERFLOW.
+// Two kernels.  migrate_kernel: one warp per tile (four tiles per CTA) reads
+// each entry of the tile's outbox once, works out the tile its cell lies in
+// (one of the 8 neighbours: particles move at most one cell per step,
+// Sec. 3.2) and appends it to that tile's arrivals, behind its stayers: the
+// lanes bound for the same tile find each other with __match_any_sync and
+// one of them claims their slots with one atomic add on the tile's arrival
+// counter.  Tiles in the last column also receive the new plasma column
+// when the window shifts, in slots claimed the same way.  Particles that
+// find no room go to the overflow buffer and raise ERR_OVERFLOW.
+// fold_arrivals_kernel then adds every tile's arrivals to its particle
+// count (at most its capacity) and clears the counter.  The order of the
+// arrivals within a tile follows the order of the atomic adds; nothing
+// computed depends on it (the current is an exact integer sum, and every
+// particle is pushed on its own).
 
 template <typename R>
 __device__ __forceinline__ void park(OverflowDev<R> &ovf, BatchStatus *st,
@@ -59,11 +63,8 @@ __device__ __forceinline__ double window_density(const SpeciesDev<R> &P,
   return P.n0;
 }
 
-constexpr int kMigE = 8;  // outbox entries per thread and pass
-// 128 threads per tile: 8 CTAs per SM at 64 registers, so twice the tiles
-// wait on memory at once than with 256
 constexpr int kPT_MIG = 128;
-constexpr int kWarpsMig = kPT_MIG / 32;
+constexpr int kWarpsMig = kPT_MIG / 32;  // tiles per CTA
 
 // Exclusive prefix sum of v over the CTA (NT threads); total = sum.
 template <int NT>
@@ -96,147 +97,72 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum,
 template <typename R>
 __global__ void __launch_bounds__(kPT_MIG)
     migrate_kernel(const SimDev<R> *__restrict__ sims,
-                   const int2 *__restrict__ items, BatchStatus *st,
-                   OverflowDev<R> ovf) {
-  __shared__ int nbl[8];
-  __shared__ int nnb;
-  // per species: the neighbours' outbox counts, then their prefix; the
-  // tile's stayer count, capacity and segment offset
-  __shared__ int pre[kMaxSpecies][9];
-  __shared__ int tcnt[kMaxSpecies], tcap[kMaxSpecies];
-  __shared__ int toff[kMaxSpecies];
-  __shared__ int wsum[kWarpsMig];
-  __shared__ int klist[kPT_MIG * kMigE];  // kept outbox entries of a pass
-  __shared__ int cursor;
-  const int step = st->step;
-  if (frozen(st, step)) return;
-  const int2 it = items[blockIdx.x];
-  const SimDev<R> &S = sims[it.x];
-  const int tile = it.y;
-  const int tcx = tile % S.ntx, tcy = tile / S.ntx;
-  const int x0 = tcx * S.tx, y0 = tcy * S.ty;
-  const int tw = min(S.tx, S.nx - x0), th = min(S.ty, S.ny - y0);
-  if (threadIdx.x == 0) {
-    int m = 0;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (!dx && !dy) continue;
-        int cx = tcx + dx;
-        const int cy = wrap1(tcy + dy, S.nty);
-        if (S.open_x) {
-          if (cx < 0 || cx >= S.ntx) continue;
-        } else {
-          cx = wrap1(cx, S.ntx);
-        }
-        const int nb = cy * S.ntx + cx;
-        bool dup = nb == tile;
-        for (int q = 0; q < m; ++q) dup |= nbl[q] == nb;
-        if (!dup) nbl[m++] = nb;
-      }
-    nnb = m;
-  }
-  __syncthreads();
-  // every count this tile needs, for all species, in one round trip
-  for (int k = threadIdx.x; k < S.nsp * 9; k += blockDim.x) {
-    const int s = k / 9, q = k - s * 9;
-    const SpeciesDev<R> &P = S.sp[s];
-    if (q < nnb) pre[s][q + 1] = P.ob_cnt[nbl[q]];
-    if (q == 8) {
-      tcnt[s] = P.cnt[tile];
-      tcap[s] = P.cap[tile];
-      toff[s] = P.off[tile];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < S.nsp) {
-    int a = 0;
-    pre[threadIdx.x][0] = 0;
-    for (int q = 0; q < nnb; ++q) {
-      a += pre[threadIdx.x][q + 1];
-      pre[threadIdx.x][q + 1] = a;
-    }
-  }
-  const int nsh = S.moving_window ? *S.n_shift : 0;
-  const bool shift = shift_due(S, step, nsh);
-  const bool inject_col = shift && (x0 + tw == S.nx);
+                   const int2 *__restrict__ items, int n_items,
+                   BatchStatus *st, OverflowDev<R> ovf) {
+  constexpr unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-
+  const int item = blockIdx.x * kWarpsMig + (threadIdx.x >> 5);
+  if (item >= n_items) return;  // warps work alone: no block barrier
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const int2 it = items[item];
+  const SimDev<R> &S = sims[it.x];
+  const int tile = it.y;
+  const int tx = S.tx, ty = S.ty, ntx = S.ntx;
+  const int x0 = (tile % ntx) * tx, y0 = (tile / ntx) * ty;
+  const int tw = min(tx, S.nx - x0), th = min(ty, S.ny - y0);
+  const int nsh = S.moving_window ? *S.n_shift : 0;
+  const bool inject_col = shift_due(S, step, nsh) && (x0 + tw == S.nx);
   // the copy the push kernel just wrote
   const int nxt = ((step + 1) & 1) ^ *S.pswap;
   for (int s = 0; s < S.nsp; ++s) {
     const SpeciesDev<R> &P = S.sp[s];
     const Planes<R> &O = P.buf[nxt];
-    __syncthreads();
-    const int *pq = pre[s];
-    const int n_stay = tcnt[s];
-    const int cap = tcap[s];
-    const size_t base = (size_t)toff[s];
-    const int m_all = pq[nnb];
-    int placed = 0;  // arrivals placed by earlier passes (CTA-uniform)
-    // the outbox planes, read once: the copies below store to global memory,
-    // which would otherwise make the compiler reload every pointer
-    const int ob_cap = P.ob_cap;
-    const int *__restrict__ ob_ix = P.ob_ix;
-    const int *__restrict__ ob_iy = P.ob_iy;
-    for (int k0 = 0; k0 < m_all; k0 += kPT_MIG * kMigE) {
-      // pass: load the destination cells of up to kMigE entries per thread;
-      // entry k of the concatenated list is entry k - pq[q] of neighbour q
-      const auto entry = [&](int k) {
-        int q = 0;
-        while (q + 1 < nnb && pq[q + 1] <= k) ++q;
-        return nbl[q] * ob_cap + (k - pq[q]);
-      };
-      unsigned keep = 0;
-      int ent[kMigE];
-#pragma unroll
-      for (int j = 0; j < kMigE; ++j) {
-        const int k = k0 + j * kPT_MIG + threadIdx.x;
-        ent[j] = 0;
-        if (k < m_all) {
-          const int e = entry(k);
-          ent[j] = e;
-          const int ix = ob_ix[e], iy = ob_iy[e];
-          if (ix >= x0 && ix < x0 + tw && iy >= y0 && iy < y0 + th)
-            keep |= 1u << j;
-        }
+    const bool has_w = O.w != nullptr, has_id = O.id != nullptr;
+    const int n_out = P.ob_cnt[tile];
+    const size_t ob0 = (size_t)tile * P.ob_cap;
+    for (int k0 = 0; k0 < n_out; k0 += 32) {
+      const int k = k0 + lane;
+      const bool mine = k < n_out;
+      int ix = 0, iy = 0, id = 0, dest = 0;
+      R x = R(0), y = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(1);
+      if (mine) {
+        const size_t e = ob0 + k;
+        ix = P.ob_ix[e];
+        iy = P.ob_iy[e];
+        x = P.ob_x[e];
+        y = P.ob_y[e];
+        ux = P.ob_ux[e];
+        uy = P.ob_uy[e];
+        uz = P.ob_uz[e];
+        if (has_w) w = P.ob_w[e];
+        if (has_id) id = P.ob_id[e];
+        dest = (iy / ty) * ntx + ix / tx;
       }
-      int total;
-      const int first =
-          block_exclusive_scan<kPT_MIG>(__popc(keep), wsum, total);
-      // the kept entries in slot order, then one copy per thread
-      int r = first;
-#pragma unroll
-      for (int j = 0; j < kMigE; ++j)
-        if (keep & (1u << j)) klist[r++] = ent[j];
-      __syncthreads();
-      for (int q = threadIdx.x; q < total; q += kPT_MIG) {
-        const int e = klist[q];
-        const int ix = ob_ix[e], iy = ob_iy[e];
-        const R x = P.ob_x[e], y = P.ob_y[e];
-        const R ux = P.ob_ux[e], uy = P.ob_uy[e], uz = P.ob_uz[e];
-        const R w = O.w ? P.ob_w[e] : R(1);
-        const int id = O.id ? P.ob_id[e] : 0;
-        const int d = n_stay + placed + q;
-        if (d < cap) {
-          const size_t t = base + d;
-          O.cell[t] = local_cell(ix - x0, iy - y0);
-          O.x[t] = x;
-          O.y[t] = y;
-          O.ux[t] = ux;
-          O.uy[t] = uy;
-          O.uz[t] = uz;
-          if (O.w) O.w[t] = w;
-          if (O.id) O.id[t] = id;
-        } else {
-          park(ovf, st, step, it.x, s, ix, iy, id, x, y, ux, uy, uz, w);
-        }
+      // lanes without an entry get keys of their own
+      const unsigned peers = __match_any_sync(kAll, mine ? dest : -1 - lane);
+      if (!mine) continue;
+      const int leader = __ffs(peers) - 1;
+      int slot = 0;
+      if (lane == leader) slot = atomicAdd(P.arr + dest, __popc(peers));
+      slot = __shfl_sync(peers, slot, leader) + __popc(peers & lt);
+      const int d = P.cnt[dest] + slot;
+      if (d < P.cap[dest]) {
+        const size_t t = (size_t)P.off[dest] + d;
+        const int dx0 = (dest % ntx) * tx, dy0 = (dest / ntx) * ty;
+        O.cell[t] = local_cell(ix - dx0, iy - dy0);
+        O.x[t] = x;
+        O.y[t] = y;
+        O.ux[t] = ux;
+        O.uy[t] = uy;
+        O.uz[t] = uz;
+        if (has_w) O.w[t] = w;
+        if (has_id) O.id[t] = id;
+      } else {
+        park(ovf, st, step, it.x, s, ix, iy, id, x, y, ux, uy, uz, w);
       }
-      placed += total;
-      __syncthreads();  // klist is refilled by the next pass
     }
-    if (threadIdx.x == 0) cursor = placed;
-    __syncthreads();
     // moving window: cold plasma on a lattice enters through column nx-1
     if (inject_col && P.inj_ppc_x > 0) {
       const int ppx = P.inj_ppc_x, ppc = ppx * P.inj_ppc_y;
@@ -245,40 +171,62 @@ __global__ void __launch_bounds__(kPT_MIG)
       const double dens = window_density(P, xa);
       if (dens > 0.0) {
         const int total = th * ppc;
-        for (int k0 = 0; k0 < total; k0 += blockDim.x) {
-          const int k = k0 + threadIdx.x;
-          const bool mine = k < total;
-          const unsigned bal = __ballot_sync(0xffffffffu, mine);
-          const int leader = __ffs(bal) - 1;
-          int wb = 0;
-          if (lane == leader) wb = atomicAdd(&cursor, __popc(bal));
-          wb = __shfl_sync(0xffffffffu, wb, leader);
-          if (!mine) continue;
+        int s0 = 0;
+        if (lane == 0) s0 = atomicAdd(P.arr + tile, total);
+        s0 = __shfl_sync(kAll, s0, 0);
+        const int n_stay = P.cnt[tile], cap = P.cap[tile];
+        const size_t base = (size_t)P.off[tile];
+        for (int k = lane; k < total; k += 32) {
           const int j = y0 + k / ppc, kk = k % ppc;
           const int kx = kk % ppx, ky = kk / ppx;
-          const R x = (R)((kx + 0.5) / ppx), y = (R)((ky + 0.5) / P.inj_ppc_y);
-          const int id =
+          const R px = (R)((kx + 0.5) / ppx);
+          const R py = (R)((ky + 0.5) / P.inj_ppc_y);
+          const int pid =
               (int)(P.id_base + ((long long)nsh * S.ny + j) * ppc + kk);
-          const int d = n_stay + wb + __popc(bal & lt);
+          const int d = n_stay + s0 + k;
           if (d < cap) {
             const size_t t = base + d;
             O.cell[t] = local_cell(i - x0, j - y0);
-            O.x[t] = x;
-            O.y[t] = y;
+            O.x[t] = px;
+            O.y[t] = py;
             O.ux[t] = R(0);
             O.uy[t] = R(0);
             O.uz[t] = R(0);
-            if (O.w) O.w[t] = (R)dens;
-            if (O.id) O.id[t] = id;
+            if (has_w) O.w[t] = (R)dens;
+            if (has_id) O.id[t] = pid;
           } else {
-            park(ovf, st, step, it.x, s, i, j, id, x, y, R(0), R(0), R(0),
+            park(ovf, st, step, it.x, s, i, j, pid, px, py, R(0), R(0), R(0),
                  (R)dens);
           }
         }
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) P.cnt[tile] = min(n_stay + cursor, cap);
+  }
+}
+
+// Every tile's arrivals join its particle count (those beyond its capacity
+// went to the overflow buffer), and the arrival counters start the next
+// step at zero.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    fold_arrivals_kernel(const SimDev<R> *__restrict__ sims,
+                         const int2 *__restrict__ items, int n_items,
+                         BatchStatus *st) {
+  const int step = st->step;
+  if (frozen(st, step)) return;
+  const long long n = (long long)n_items * kMaxSpecies;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / kMaxSpecies), s = (int)(q - (long long)i * kMaxSpecies);
+    const int2 it = items[i];
+    const SimDev<R> &S = sims[it.x];
+    if (s >= S.nsp) continue;
+    const SpeciesDev<R> &P = S.sp[s];
+    const int a = P.arr[it.y];
+    if (a != 0) {
+      P.cnt[it.y] = min(P.cnt[it.y] + a, P.cap[it.y]);
+      P.arr[it.y] = 0;
+    }
   }
 }
 
@@ -287,7 +235,15 @@ cudaError_t launch_migrate(const SimDev<R> *sims, const int2 *items,
                            int n_items, BatchStatus *st,
                            const OverflowDev<R> &ovf, cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
-  migrate_kernel<R><<<n_items, kPT_MIG, 0, stream>>>(sims, items, st, ovf);
+  migrate_kernel<R><<<(n_items + kWarpsMig - 1) / kWarpsMig, kPT_MIG, 0,
+                      stream>>>(sims, items, n_items, st, ovf);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)n_items * kMaxSpecies;
+  const int grid = (int)std::min<long long>((n + kThreads - 1) / kThreads,
+                                            152 * 8);
+  fold_arrivals_kernel<R><<<grid, kThreads, 0, stream>>>(sims, items, n_items,
+                                                          st);
   return cudaGetLastError();
 }
 

@@ -273,7 +273,7 @@ struct SpeciesHost {
   double w_max = 0.0;    // largest weight given through set_particles
   long long total_cap = 0;
   DevMem store[2];                              // two copies of the store
-  DevMem off, cap, cnt, ob_cnt;                 // per tile
+  DevMem off, cap, cnt, ob_cnt, arr;            // per tile
   DevMem ob_ix, ob_iy, ob_id, ob_x, ob_y, ob_ux, ob_uy, ob_uz, ob_w;
   int ob_cap = 0;
   std::vector<int> h_cnt;                       // last counts read
@@ -1222,9 +1222,11 @@ class Batch : public BatchBase {
     }
     if (!P.off.p) {
       if (!dalloc(P.off, 4 * S.ntiles) || !dalloc(P.cap, 4 * S.ntiles) ||
-          !dalloc(P.cnt, 4 * S.ntiles) || !dalloc(P.ob_cnt, 4 * S.ntiles))
+          !dalloc(P.cnt, 4 * S.ntiles) || !dalloc(P.ob_cnt, 4 * S.ntiles) ||
+          !dalloc(P.arr, 4 * S.ntiles))
         return fail(ZPIC_ENOMEM, "tile tables");
       ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
+      ZP_CU(cudaMemsetAsync(P.arr.p, 0, 4 * S.ntiles, stream_));
     }
     if (!P.ob_ix.p) {  // outbox planes (again after the outbox grew)
       const size_t nob = (size_t)P.ob_cap * S.ntiles;
@@ -1268,6 +1270,7 @@ class Batch : public BatchBase {
     Q.cap = (int *)P.cap.p;
     Q.cnt = (int *)P.cnt.p;
     Q.ob_cnt = (int *)P.ob_cnt.p;
+    Q.arr = (int *)P.arr.p;
     Q.ob_ix = (int *)P.ob_ix.p;
     Q.ob_iy = (int *)P.ob_iy.p;
     Q.ob_id = (int *)P.ob_id.p;
@@ -1485,6 +1488,7 @@ class Batch : public BatchBase {
                        full_tile_cap(nominal, slack, window_plasma(S, P))));
     ZP_CU(cudaMemsetAsync(P.cnt.p, 0, 4 * S.ntiles, stream_));
     ZP_CU(cudaMemsetAsync(P.ob_cnt.p, 0, 4 * S.ntiles, stream_));
+    ZP_CU(cudaMemsetAsync(P.arr.p, 0, 4 * S.ntiles, stream_));
     if (ready) ZP_CU(cudaStreamWaitEvent(stream_, ready, 0));
     int pc = 0;
     ZP_TRY(particle_copy(si, &pc));
@@ -1734,7 +1738,7 @@ class Batch : public BatchBase {
       for (auto &S : sims_) {
         for (auto &P : S.sp)
           for (DevMem *m : {&P.store[0], &P.store[1], &P.off, &P.cap, &P.cnt,
-                            &P.ob_cnt, &P.ob_ix,
+                            &P.ob_cnt, &P.arr, &P.ob_ix,
                             &P.ob_iy, &P.ob_id, &P.ob_x, &P.ob_y, &P.ob_ux,
                             &P.ob_uy, &P.ob_uz, &P.ob_w})
             dfree(*m);

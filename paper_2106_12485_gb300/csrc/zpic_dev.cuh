@@ -86,6 +86,7 @@ struct SpeciesDev {
   int *off, *cap, *cnt;            // per tile
   int ob_cap;                      // outbox slots per tile
   int *ob_cnt;                     // per tile
+  int *arr;                        // per tile: arrivals claimed this step
   int *ob_ix, *ob_iy, *ob_id;
   R *ob_x, *ob_y, *ob_ux, *ob_uy, *ob_uz, *ob_w;
   // moving-window injection of cold plasma on a lattice
