@@ -1161,6 +1161,18 @@ class Batch : public BatchBase {
     SimHost<R> &S = sims_[si];
     SpeciesHost<R> &P = S.sp[s];
     std::vector<int> off(S.ntiles), cap(S.ntiles);
+    // plasma flowing through a moving window meets the same wake in every
+    // tile it reaches: once a tile has been compressed beyond the room every
+    // tile gets, every tile gets room for that tile's count plus the slack,
+    // so the wake does not overflow each new tile it reaches in turn (a
+    // re-sort per few tens of steps on the 4096 x 512 LWFA while its window
+    // fills; room as if the whole window held the densest tile's plasma)
+    if (window_plasma(S, P)) {
+      int mx = 0;
+      for (int t = 0; t < S.ntiles; ++t) mx = std::max(mx, cnt[t]);
+      if (mx > min_cap)
+        min_cap = (int)std::min<double>(INT_MAX / 2, std::ceil(mx * (1.0 + slack)));
+    }
     // densest tile within two tiles of each tile (a compressed structure
     // moving through the tiles reaches its neighbours next)
     std::vector<int> near(S.ntiles, 0);
