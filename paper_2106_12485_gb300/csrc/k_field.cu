@@ -2,11 +2,12 @@
 // laser initialisation (Sec. 4.1), and the end-of-step bookkeeping
 // (energy records, moving-window counter, step counter).
 //
-// Yee step, one CTA per 32 x 8 block of cells, temporal blocking of the three
-// sub-steps inside the block:
-//   load E^n on [-1, 33] x [-1, 9], B^n on [-1, 32] x [-1, 8], J on [0, 32]^2
-//   B^{n+1/2} = B^n - (dt/2) curl E^n        on [-1, 32] x [-1, 8]
-//   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J) on [0, 32] x [0, 8]
+// Yee step, one CTA (256 threads) per 32 x 16 block of cells, temporal
+// blocking of the three sub-steps inside the block:
+//   load E^n on [-1, 33] x [-1, 17], B^n on [-1, 32] x [-1, 16],
+//        J on [0, 32] x [0, 16]
+//   B^{n+1/2} = B^n - (dt/2) curl E^n        on [-1, 32] x [-1, 16]
+//   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J) on [0, 32] x [0, 16]
 //   B^{n+1}   = B^{n+1/2} - (dt/2) curl E^{n+1} on the block's own cells
 // and writes E^{n+1}, B^{n+1} of its own cells to the other field copy, one
 // cell to the left when the moving window shifts this step.  HBM traffic per
@@ -324,10 +325,13 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
 
-  // B^{n+1} on the block's own cells (one per thread) and write back
-  const int i = threadIdx.x % X, j = threadIdx.x / X;
-  const int gi = x0 + i, gj = y0 + j;
+  // B^{n+1} on the block's own cells (X * Y / kThreads per thread) and
+  // write back
   R e2 = R(0), b2 = R(0);
+#pragma unroll
+  for (int r = threadIdx.x; r < X * Y; r += kThreads) {
+  const int i = r % X, j = r / X;
+  const int gi = x0 + i, gj = y0 + j;
   if (gi < S.nx && gj < S.ny) {
     const R ez = se[2][j + 1][i + 1];
     const R nbx = sb[0][j + 1][i + 1] - h * (se[2][j + 2][i + 1] - ez) * rdy;
@@ -337,8 +341,8 @@ __global__ void __launch_bounds__(kThreads)
                        (se[0][j + 2][i + 1] - se[0][j + 1][i + 1]) * rdy);
     const R ex = se[0][j + 1][i + 1], ey = se[1][j + 1][i + 1];
     if (do_energy) {
-      e2 = ex * ex + ey * ey + ez * ez;
-      b2 = nbx * nbx + nby * nby + nbz * nbz;
+      e2 += ex * ex + ey * ey + ez * ez;
+      b2 += nbx * nbx + nby * nby + nbz * nbz;
     }
     const size_t row = (size_t)gj * S.ld;
     const int wi = gi - shift;
@@ -363,15 +367,16 @@ __global__ void __launch_bounds__(kThreads)
         S.J[nxt][c][row + gi] = R(0);
     }
   }
+  }
   if (do_energy)
     block_sum2_store(e2, b2, red, S.part_fld + (size_t)it.y * 2);
 }
 
 // Compensated binomial filter of the current (optional; Sec. 2.2 digital
 // filter on J, Sec. 4.1 LWFA runs): per component and per axis, x then y,
-// one (1, 2, 1)/4 pass and one (-1, 6, -1)/4 pass.  One CTA per 32 x 8
-// block: J on [-2, 34) x [-2, 10) in shared memory, the two x passes on all
-// 12 rows, the two y passes on the block's rows; with an open x boundary
+// one (1, 2, 1)/4 pass and one (-1, 6, -1)/4 pass.  One CTA per 32 x 16
+// block: J on [-2, 34) x [-2, 18) in shared memory, the two x passes on all
+// 20 rows, the two y passes on the block's rows; with an open x boundary
 // every pass reads zero outside [0, nx), as if each pass were a separate
 // sweep over the grid.  Writes Jf, which the Yee kernel then reads.
 template <typename R>
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(kThreads)
                   const int2 *__restrict__ items, BatchStatus *st) {
   constexpr int X = kYeeX, Y = kYeeY;
   constexpr int W = X + 4, H = Y + 4;
-  static_assert(X * Y == kThreads, "one thread per output cell");
+  static_assert(X * Y % kThreads == 0, "whole output cells per thread");
   __shared__ R a[H][W];       // J, then the compensated x pass
   __shared__ R b[H][W];       // binomial x pass, then binomial y pass
   const int step = st->step;
@@ -420,8 +425,8 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
     // y compensation on the block's own rows, written out
-    {
-      const int i = threadIdx.x % X, j = threadIdx.x / X;
+    for (int r = threadIdx.x; r < X * Y; r += kThreads) {
+      const int i = r % X, j = r / X;
       const int gi = x0 + i, gj = y0 + j;
       const int li = i + 2, lj = j + 2;
       const R v = -q * b[lj - 1][li] + c15 * b[lj][li] - q * b[lj + 1][li];
