@@ -427,10 +427,12 @@ __device__ __forceinline__ void block_sum_store(double v, double *dst,
 
 // A particle that leaves its tile goes to the tile's outbox (global cell
 // index), or, when the outbox is full, to the overflow buffer that the host
-// drains by re-sorting.  Out of line: few particles take this path, and its
-// pointers would otherwise occupy registers in the particle loop.
+// drains by re-sorting.  Inlined: a call in the particle loop, even one
+// that few lanes take, cost 3 % of the kernel's time (measured on the
+// 2048^2 plasma: 8.94 against 9.22 ms per launch), and the loop still fits
+// its 80 registers without spills.
 template <typename R>
-__device__ __noinline__ void park_leaver(const SpeciesDev<R> &P,
+__device__ __forceinline__ void park_leaver(const SpeciesDev<R> &P,
                                          const OverflowDev<R> &ovf,
                                          BatchStatus *st, int tile, int slot,
                                          int sim, int s, int step, int nix,
