@@ -362,6 +362,26 @@ def fp32_over_fp64(args, stream, torch, fp32_value, steps=5):
             "ratio": fp32_value / v64}
 
 
+def tune_batch_and_sims(cfgs, Z, steps=10):
+    """The autotuner's settings for both forms of a sweep: the batch as a
+    whole (zpic_batch_autotune; Batch(cfgs) then uses them) and each
+    simulation's class for the per-simulation launches (zpic_autotune; Sim
+    uses its tile).  Returns a summary of the choices."""
+    out = {}
+    if len(cfgs) >= 2:
+        t, _ = Z.batch_autotune(cfgs, steps=steps)
+        out["batch"] = {"tile": [t.tile_x, t.tile_y],
+                        "ctas_per_sm": t.push_ctas_per_sm,
+                        "sort_every": t.sort_every}
+    tiles = {}
+    for c in cfgs:
+        tx, ty, _ = Z.autotune(c, steps=4)
+        key = "%dx%d" % (tx, ty)
+        tiles[key] = tiles.get(key, 0) + 1
+    out["per_sim_tiles"] = tiles
+    return out
+
+
 def batched_over_per_sim(args, stream, torch, steps=10):
     """The batched sweep (256 independent simulations, one persistent
     launch per stage, captured in a CUDA graph) against the same simulations
@@ -370,6 +390,7 @@ def batched_over_per_sim(args, stream, torch, steps=10):
     from paper_2106_12485_gb300 import zpic as Z
     from synthetic import plasma as P
     cfgs = W.batch_sweep(P.batch_specs(256))
+    tuning = tune_batch_and_sims(cfgs, Z, steps)
     batch = Z.Batch(cfgs)
     batch.set_stream(stream.cuda_stream)
     batch.step(3)
@@ -402,7 +423,7 @@ def batched_over_per_sim(args, stream, torch, steps=10):
     return {"sims": len(cfgs), "particles": int(n), "steps": steps,
             "batched_value": n * steps / (ms_b / 1e3),
             "per_sim_value": n * steps / (ms_s / 1e3),
-            "ratio": ms_s / ms_b}
+            "ratio": ms_s / ms_b, "tuning": tuning}
 
 
 def rel_l2(a, b):
@@ -536,6 +557,7 @@ def batch_workload(args, rank, world):
     parts = W.lpt_partition(W.batch_costs(specs), world)
     mine = set(parts[rank])
     cfgs = [c for i, c in enumerate(W.batch_sweep(specs)) if i in mine]
+    tuning = tune_batch_and_sims(cfgs, Z)
     batch = Z.Batch(cfgs)
     batch.set_stream(stream.cuda_stream)
     batch.step(args.warmup)
@@ -580,7 +602,7 @@ def batch_workload(args, rank, world):
             per_sim_launches={"value": value_s,
                               "ms_per_step": ms_s_max / args.steps},
             batched_over_per_sim=ms_s_max / ms_b_max,
-            kernels_ms_next_steps=split)))
+            kernels_ms_next_steps=split, tuning=tuning)))
     else:
         all_sum(float(n), world)
 

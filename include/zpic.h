@@ -445,6 +445,25 @@ typedef struct {
 int zpic_autotune_all(const zpic_config *cfg, int steps, zpic_tuning *best,
                       double *ms_per_candidate, int cap, int *n_candidates);
 
+/* Tunes the same three settings for a batch of n >= 2 simulations (the
+ * batched sweep: many independent simulations advanced by one launch per
+ * stage, Sec. 3.2's regions over all of them), by timing the batch itself
+ * with each candidate given to every member, in the order of
+ * zpic_autotune_all: the tile candidates at `steps` timed steps after 3,
+ * then the resident CTAs per SM, then the re-sort intervals over 80 steps
+ * after 40.  The full batch is created and destroyed once per candidate
+ * (its memory and time are those of the batch).  The choice is kept for
+ * this list of configuration classes, and zpic_batch_create with the same
+ * list uses it for the settings its members leave at 0; without it those
+ * members get 16 x 16 tiles, not the per-class choices of zpic_autotune,
+ * which are made for a simulation alone on the GPU.  ms_per_candidate and
+ * n_candidates as for zpic_autotune_all.  ZPIC_EINVAL for NULL arguments,
+ * n < 2 or steps outside [1, 10000]; ZPIC_ECUDA when no tile candidate
+ * ran. */
+int zpic_batch_autotune(const zpic_config *cfgs, int n, int steps,
+                        zpic_tuning *best, double *ms_per_candidate, int cap,
+                        int *n_candidates);
+
 /* Kernel timing: when enabled, zpic_step launches kernels one by one and
  * records a CUDA event pair around each launch on the handle's stream.
  * zpic_profile_read returns, per kernel name, the summed device time (ms)

@@ -14,6 +14,13 @@
 // and momenta; profiles, window and laser placed at the same distance from
 // the right edge), keep the fastest per configuration class, and
 // zpic_create uses the choice for settings a configuration leaves at 0.
+// zpic_batch_autotune tunes the same three settings for a whole batch, by
+// timing the batch itself with each candidate applied to every member: one
+// batched launch per stage runs one tile size (the 16 x 16 one compiled
+// for it), and the per-class choices, made for a simulation that has the
+// GPU to itself, favour small tiles that fill the GPU with one small grid
+// (measured on the 256-simulation sweep: per-class tiles, 223 of them
+// 8 x 8, made its particle kernel 1.7 times slower than 16 x 16 for all).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +30,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/zpic.h"
 
@@ -41,6 +49,7 @@ constexpr int kMaxSide = 1024;
 std::mutex g_mu;
 std::map<std::string, std::pair<int, int>> g_tuned;
 std::map<std::string, zpic_tuning> g_tuned_all;
+std::map<std::string, zpic_tuning> g_tuned_batch;
 
 // The class of a configuration: what decides the best tile size is the
 // precision, the particles per cell of each species (the work per tile),
@@ -102,6 +111,32 @@ double time_candidate(const zpic_config &r, int steps, int warm = 3) {
   return ms;
 }
 
+// A batch's key: its members' classes in order.
+std::string batch_key(const zpic_config *cfgs, int n) {
+  std::string k = "batch " + std::to_string(n);
+  for (int i = 0; i < n; ++i) k += " | " + class_key(cfgs[i]);
+  return k;
+}
+
+// Host wall time per step of the whole batch with `steps` timed steps
+// after `warm`, or a negative value if it cannot run.
+double time_batch(const std::vector<zpic_config> &cfgs, int steps,
+                  int warm = 3) {
+  zpic_batch *b = nullptr;
+  if (zpic_batch_create(cfgs.data(), (int)cfgs.size(), &b) != ZPIC_OK)
+    return -1.0;
+  double ms = -1.0;
+  if (zpic_batch_step(b, warm) == ZPIC_OK && zpic_batch_sync(b) == ZPIC_OK) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (zpic_batch_step(b, steps) == ZPIC_OK && zpic_batch_sync(b) == ZPIC_OK) {
+      const auto t1 = std::chrono::steady_clock::now();
+      ms = std::chrono::duration<double, std::milli>(t1 - t0).count() / steps;
+    }
+  }
+  zpic_batch_destroy(b);
+  return ms;
+}
+
 const int kCand[][2] = {{16, 16}, {8, 8}, {12, 12}, {24, 24}, {32, 32},
                         {32, 16}, {16, 32}};
 constexpr int kNCand = sizeof(kCand) / sizeof(kCand[0]);
@@ -113,6 +148,15 @@ constexpr int kSortWarm = 40, kSortSteps = 80;
 }  // namespace
 
 namespace zp {
+// The settings zpic_batch_autotune chose for this batch, if it has run.
+bool tuned_batch(const zpic_config *cfgs, int n, zpic_tuning *t) {
+  std::lock_guard<std::mutex> g(g_mu);
+  auto it = g_tuned_batch.find(batch_key(cfgs, n));
+  if (it == g_tuned_batch.end()) return false;
+  *t = it->second;
+  return true;
+}
+
 // The settings zpic_autotune_all chose for c's class, if it has run.
 bool tuned_setting(const zpic_config &c, zpic_tuning *t) {
   std::lock_guard<std::mutex> g(g_mu);
@@ -253,6 +297,87 @@ int zpic_autotune_all(const zpic_config *cfg, int steps, zpic_tuning *best,
     std::lock_guard<std::mutex> g(g_mu);
     g_tuned[key] = {bx, by};
     g_tuned_all[key] = t;
+  }
+  *best = t;
+  return ZPIC_OK;
+}
+
+int zpic_batch_autotune(const zpic_config *cfgs, int n, int steps,
+                        zpic_tuning *best, double *ms_per_candidate, int cap,
+                        int *n_candidates) {
+  if (!cfgs || !best) return zp::set_last_error(ZPIC_EINVAL, "NULL argument");
+  if (n < 2) return zp::set_last_error(ZPIC_EINVAL, "a batch has 2 or more simulations");
+  if (steps < 1 || steps > 10000)
+    return zp::set_last_error(ZPIC_EINVAL, "steps out of range");
+  const int n_cta = cfgs[0].precision == ZPIC_FP64 ? 2 : 3;
+  const int n_sort = (int)(sizeof(kSortCand) / sizeof(kSortCand[0]));
+  if (n_candidates) *n_candidates = kNCand + n_cta + n_sort;
+  int k_out = 0;
+  auto record = [&](double ms) {
+    if (ms_per_candidate && k_out < cap) ms_per_candidate[k_out] = ms;
+    ++k_out;
+  };
+  // every member gets the candidate; energy records are not needed
+  std::vector<zpic_config> v(cfgs, cfgs + n);
+  for (auto &c : v) {
+    c.energy_every = 0;
+    c.flags &= ~ZPIC_TRACK_IDS;
+    c.sort_every = -1;
+    c.push_ctas_per_sm = 0;
+  }
+  double bt = -1.0;
+  int bx = 16, by = 16;
+  for (int k = 0; k < kNCand; ++k) {
+    for (auto &c : v) {
+      c.tile_x = kCand[k][0];
+      c.tile_y = kCand[k][1];
+    }
+    const double ms = time_batch(v, steps);
+    record(ms);
+    if (ms > 0 && (bt < 0 || ms < bt)) {
+      bt = ms;
+      bx = kCand[k][0];
+      by = kCand[k][1];
+    }
+  }
+  if (bt < 0)
+    return zp::set_last_error(ZPIC_ECUDA, "no tile size candidate could run");
+  for (auto &c : v) {
+    c.tile_x = bx;
+    c.tile_y = by;
+  }
+  double bc = -1.0;
+  int ctas = 0;
+  for (int k = 0; k < n_cta; ++k) {
+    for (auto &c : v) c.push_ctas_per_sm = kCtaCand[k];
+    const double ms = time_batch(v, steps);
+    record(ms);
+    if (ms > 0 && (bc < 0 || ms < bc)) {
+      bc = ms;
+      ctas = kCtaCand[k];
+    }
+  }
+  for (auto &c : v) c.push_ctas_per_sm = ctas;
+  double bs = -1.0;
+  int sort = -1;
+  for (int k = 0; k < n_sort; ++k) {
+    for (auto &c : v) c.sort_every = kSortCand[k];
+    const double ms = time_batch(v, kSortSteps, kSortWarm);
+    record(ms);
+    if (ms > 0 && (bs < 0 || ms < bs)) {
+      bs = ms;
+      sort = kSortCand[k];
+    }
+  }
+  zpic_tuning t{};
+  t.tile_x = bx;
+  t.tile_y = by;
+  t.push_ctas_per_sm = ctas;
+  t.sort_every = sort;
+  t.ms_per_step = bs;
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    g_tuned_batch[batch_key(cfgs, n)] = t;
   }
   *best = t;
   return ZPIC_OK;

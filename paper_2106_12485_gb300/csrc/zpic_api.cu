@@ -45,6 +45,7 @@ namespace zp {
 int set_last_error(int code, const char *msg) { return fail(code, msg); }
 bool tuned_tile(const zpic_config &c, int *tx, int *ty);  // autotune.cu
 bool tuned_setting(const zpic_config &c, zpic_tuning *t);  // autotune.cu
+bool tuned_batch(const zpic_config *cfgs, int n, zpic_tuning *t);  // autotune.cu
 }  // namespace zp
 
 static int cuda_fail(cudaError_t e, const char *what) {
@@ -1817,6 +1818,29 @@ int make_batch(const zpic_config *cfgs, int n, zpic_batch **out) {
   for (int i = 1; i < n; ++i)
     if (cfgs[i].precision != cfgs[0].precision)
       return fail(ZPIC_EINVAL, "all sims of a batch share one precision");
+  // Members of a batch (two or more simulations) that leave a setting at 0
+  // take the batch's tuning (zpic_batch_autotune) if it has run, else a
+  // 16 x 16 tile (the batched kernel compiled for it) and the other
+  // settings as for a single simulation.  The per-class tile sizes of
+  // zpic_autotune are not used here: they are chosen for a simulation that
+  // has the GPU to itself, and a batch whose members differ in tile size
+  // runs the slower generic kernel.
+  std::vector<zpic_config> own;
+  if (n > 1) {
+    own.assign(cfgs, cfgs + n);
+    zpic_tuning t{};
+    const bool tuned = tuned_batch(cfgs, n, &t);
+    for (auto &c : own) {
+      if (c.tile_x == 0 && c.tile_y == 0) {
+        c.tile_x = tuned ? t.tile_x : 16;
+        c.tile_y = tuned ? t.tile_y : 16;
+      }
+      if (tuned && c.sort_every == 0) c.sort_every = t.sort_every;
+      if (tuned && c.push_ctas_per_sm == 0)
+        c.push_ctas_per_sm = t.push_ctas_per_sm;
+    }
+    cfgs = own.data();
+  }
   std::unique_ptr<zpic_batch> b(new zpic_batch);
   if (cfgs[0].precision == ZPIC_FP64)
     b->impl.reset(new Batch<double>());

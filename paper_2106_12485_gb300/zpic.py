@@ -137,6 +137,9 @@ _PROTOS = {
     "zpic_autotune_all": (C.c_int, [C.POINTER(zpic_config), C.c_int,
                                     C.POINTER(zpic_tuning), _P, C.c_int,
                                     C.POINTER(C.c_int)]),
+    "zpic_batch_autotune": (C.c_int, [C.POINTER(zpic_config), C.c_int,
+                                      C.c_int, C.POINTER(zpic_tuning), _P,
+                                      C.c_int, C.POINTER(C.c_int)]),
     "zpic_profile_enable": (C.c_int, [_P, C.c_int]),
     "zpic_profile_read": (C.c_int, [_P, _P, C.c_size_t, _P, _P, C.c_int,
                                     C.POINTER(C.c_int), C.c_int]),
@@ -496,6 +499,32 @@ def load_checkpoint(cfg, path):
              if "p%d_%s" % (s, k) in d}
         sim.set_particles(s, p)
     return sim
+
+
+def _tuning_labels(n_tiles, n_total):
+    n = lib().zpic_autotune_candidates(None, 0)
+    xy = np.zeros(2 * n, np.int32)
+    lib().zpic_autotune_candidates(_ptr(xy), n)
+    n_cta = n_total - n - 4
+    return ([("tile", (int(xy[2 * k]), int(xy[2 * k + 1]))) for k in range(n)] +
+            [("ctas_per_sm", k + 1) for k in range(n_cta)] +
+            [("sort_every", v) for v in (-1, 10, 20, 40)])
+
+
+def batch_autotune(cfgs, steps=10):
+    """Tile size, resident CTAs per SM and re-sort interval for the batch of
+    cfgs as a whole (zpic_batch_autotune), which Batch(cfgs) then uses for
+    settings left at 0: (zpic_tuning, list of (stage, candidate, ms per
+    step) in the order they were timed)."""
+    arr = (zpic_config * len(cfgs))(*cfgs)
+    ms = np.zeros(64)
+    t = zpic_tuning()
+    nc = C.c_int()
+    check(lib().zpic_batch_autotune(arr, len(cfgs), steps, C.byref(t),
+                                    _ptr(ms), ms.size, C.byref(nc)),
+          "zpic_batch_autotune")
+    labels = _tuning_labels(0, nc.value)
+    return t, [(a, b, float(ms[k])) for k, (a, b) in enumerate(labels)]
 
 
 class Batch:
