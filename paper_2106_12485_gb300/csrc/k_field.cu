@@ -2,12 +2,13 @@
 // laser initialisation (Sec. 4.1), and the end-of-step bookkeeping
 // (energy records, moving-window counter, step counter).
 //
-// Yee step, one CTA (256 threads) per 32 x 16 block of cells, temporal
-// blocking of the three sub-steps inside the block:
-//   load E^n on [-1, 33] x [-1, 17], B^n on [-1, 32] x [-1, 16],
-//        J on [0, 32] x [0, 16]
-//   B^{n+1/2} = B^n - (dt/2) curl E^n        on [-1, 32] x [-1, 16]
-//   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J) on [0, 32] x [0, 16]
+// Yee step, one CTA (256 threads) per 32 x Y block of cells (Y = 32 in
+// FP32, 16 in FP64), temporal blocking of the three sub-steps inside the
+// block:
+//   load E^n on [-1, 33] x [-1, Y+1], B^n on [-1, 32] x [-1, Y],
+//        J on [0, 32] x [0, Y]
+//   B^{n+1/2} = B^n - (dt/2) curl E^n        on [-1, 32] x [-1, Y]
+//   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J) on [0, 32] x [0, Y]
 //   B^{n+1}   = B^{n+1/2} - (dt/2) curl E^{n+1} on the block's own cells
 // and writes E^{n+1}, B^{n+1} of its own cells to the other field copy, one
 // cell to the left when the moving window shifts this step.  HBM traffic per
@@ -167,10 +168,10 @@ __device__ __forceinline__ void block_sum2_store(R e, R b, double *red,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     yee_kernel(const SimDev<R> *__restrict__ sims,
                const int2 *__restrict__ items, BatchStatus *st) {
-  constexpr int X = kYeeX, Y = kYeeY;
+  constexpr int X = kYeeX, Y = yee_rows<R>();
   constexpr int EW = X + 3, EH = Y + 3;   // E^n on [-1, X+1]
   constexpr int BW = X + 2, BH = Y + 2;   // B on [-1, X]
   constexpr int JW = X + 1, JH = Y + 1;   // J on [0, X]
@@ -374,16 +375,16 @@ __global__ void __launch_bounds__(kThreads)
 
 // Compensated binomial filter of the current (optional; Sec. 2.2 digital
 // filter on J, Sec. 4.1 LWFA runs): per component and per axis, x then y,
-// one (1, 2, 1)/4 pass and one (-1, 6, -1)/4 pass.  One CTA per 32 x 16
-// block: J on [-2, 34) x [-2, 18) in shared memory, the two x passes on all
-// 20 rows, the two y passes on the block's rows; with an open x boundary
+// one (1, 2, 1)/4 pass and one (-1, 6, -1)/4 pass.  One CTA per Yee
+// block (32 x Y): J on [-2, 34) x [-2, Y+2) in shared memory, the two x
+// passes on all Y+4 rows, the two y passes on the block's rows; with an open x boundary
 // every pass reads zero outside [0, nx), as if each pass were a separate
 // sweep over the grid.  Writes Jf, which the Yee kernel then reads.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     filter_kernel(const SimDev<R> *__restrict__ sims,
                   const int2 *__restrict__ items, BatchStatus *st) {
-  constexpr int X = kYeeX, Y = kYeeY;
+  constexpr int X = kYeeX, Y = yee_rows<R>();
   constexpr int W = X + 4, H = Y + 4;
   static_assert(X * Y % kThreads == 0, "whole output cells per thread");
   __shared__ R a[H][W];       // J, then the compensated x pass

@@ -958,7 +958,7 @@ class Batch : public BatchBase {
     S.nty = (S.ny + S.ty - 1) / S.ty;
     S.ntiles = S.ntx * S.nty;
     S.ybx = (S.nx + kYeeX - 1) / kYeeX;
-    S.yby = (S.ny + kYeeY - 1) / kYeeY;
+    S.yby = (S.ny + yee_rows<R>() - 1) / yee_rows<R>();
     const size_t plane = (size_t)S.ny * S.ld;
     const bool filter = (c.flags & ZPIC_FILTER_J) != 0;
     // E, B: 12 planes of R; J: 6 planes of 8-byte values; Jf: 3 planes of R
