@@ -455,7 +455,8 @@ cudaError_t launch_yee(const SimDev<R> *sims, const int2 *items, int n_items,
 
 // ---- end of step ----------------------------------------------------------
 
-// kEndSlices CTAs per simulation (blockIdx.x = sim * kEndSlices + slice).
+// g_max CTAs per simulation (blockIdx.x = sim * g_max + slice); slices at
+// or beyond the simulation's own count (end_g) only take the step ticket.
 // On an energy step each CTA sums its slice of the per-tile kinetic and
 // per-Yee-block field partials in compensated FP64 and stores (sum, error)
 // per quantity; the last slice of the simulation to finish (ticket)
@@ -467,18 +468,19 @@ cudaError_t launch_yee(const SimDev<R> *sims, const int2 *items, int n_items,
 // step.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    end_step_kernel(const SimDev<R> *__restrict__ sims, BatchStatus *st) {
-  constexpr int G = kEndSlices;
+    end_step_kernel(const SimDev<R> *__restrict__ sims, int g_max,
+                    BatchStatus *st) {
   __shared__ double red[kWarps * kEndQ * 2];
-  __shared__ double s_part[G * kEndQ * 2];
+  __shared__ double s_part[kEndSlicesMax * kEndQ * 2];
   __shared__ double s_q[kEndQ * 2];
   __shared__ int s_last;
   const int step = st->step;
   if (frozen(st, step)) return;
-  const int sim = blockIdx.x / G, g = blockIdx.x - sim * G;
+  const int sim = blockIdx.x / g_max, g = blockIdx.x - sim * g_max;
   const SimDev<R> &S = sims[sim];
-  const bool do_energy =
-      S.energy_every > 0 && ((step + 1) % S.energy_every) == 0;
+  const int G = S.end_g;
+  const bool do_energy = g < G && S.energy_every > 0 &&
+                         ((step + 1) % S.energy_every) == 0;
   bool owner = g == 0;
   if (do_energy) {
     const int ntiles = S.ntx * S.nty;
@@ -557,24 +559,34 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     owner = s_last != 0;
     if (owner) {
-      // every slice's values, read from L2 by all threads at once; thread k
-      // combines quantity k over the slices in slice order
+      // every slice's values, read from L2 by all threads at once; warp w
+      // combines quantity k = w, w + kWarps, ... over the slices: lane h
+      // adds slices h and h + 32, then a shuffle tree (a fixed order)
       __threadfence();
       for (int k = threadIdx.x; k < G * kEndQ * 2; k += blockDim.x)
         s_part[k] = __ldcg(S.epart + k);
       __syncthreads();
-      if (threadIdx.x < kEndQ) {
-        const int k = threadIdx.x;
+      static_assert(kEndSlicesMax <= 64, "two slices per lane");
+      for (int k = warp; k < kEndQ; k += kWarps) {
         CSum q;
-        if (used(k))
-          for (int h = 0; h < G; ++h) {
+        if (used(k)) {
+          for (int h = lane; h < G; h += 32) {
             CSum u;
             u.s = s_part[(h * kEndQ + k) * 2];
             u.c = s_part[(h * kEndQ + k) * 2 + 1];
             q.add(u);
           }
-        s_q[2 * k] = q.s;
-        s_q[2 * k + 1] = q.c;
+          for (int o = 16; o > 0; o >>= 1) {
+            CSum u;
+            u.s = __shfl_down_sync(0xffffffffu, q.s, o);
+            u.c = __shfl_down_sync(0xffffffffu, q.c, o);
+            q.add(u);
+          }
+        }
+        if (lane == 0) {
+          s_q[2 * k] = q.s;
+          s_q[2 * k + 1] = q.c;
+        }
       }
       __syncthreads();
     }
@@ -627,9 +639,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename R>
-cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
+cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims, int g_max,
                             BatchStatus *st, cudaStream_t stream) {
-  end_step_kernel<R><<<n_sims * kEndSlices, kThreads, 0, stream>>>(sims, st);
+  end_step_kernel<R><<<n_sims * g_max, kThreads, 0, stream>>>(sims, g_max,
+                                                                st);
   return cudaGetLastError();
 }
 
@@ -728,7 +741,7 @@ cudaError_t launch_laser(const SimDev<R> *sim_dev, int nx, int ny,
                                         int, BatchStatus *, cudaStream_t); \
   template cudaError_t launch_yee<R>(const SimDev<R> *, const int2 *, int, \
                                      BatchStatus *, cudaStream_t);          \
-  template cudaError_t launch_end_step<R>(const SimDev<R> *, int,          \
+  template cudaError_t launch_end_step<R>(const SimDev<R> *, int, int,     \
                                           BatchStatus *, cudaStream_t);     \
   template cudaError_t launch_laser<R>(const SimDev<R> *, int, int,        \
                                        LaserParams, cudaStream_t);          \

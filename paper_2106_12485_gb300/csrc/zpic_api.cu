@@ -1005,7 +1005,7 @@ class Batch : public BatchBase {
       D.Jf[c3] = filter ? jf + (size_t)c3 * plane : nullptr;
     if (!dalloc(S.part_kin, sizeof(double) * S.ntiles * kMaxSpecies) ||
         !dalloc(S.part_fld, sizeof(double) * 2 * S.ybx * S.yby) ||
-        !dalloc(S.epart, sizeof(double) * 2 * kEndSlices * kEndQ))
+        !dalloc(S.epart, sizeof(double) * 2 * kEndSlicesMax * kEndQ))
       return fail(ZPIC_ENOMEM, "partials");
     ZP_CU(cudaMemsetAsync(S.part_kin.p, 0, S.part_kin.bytes, stream_));
     ZP_CU(cudaMemsetAsync(S.part_fld.p, 0, S.part_fld.bytes, stream_));
@@ -1013,6 +1013,7 @@ class Batch : public BatchBase {
     D.part_fld = (double *)S.part_fld.p;
     ZP_CU(cudaMemsetAsync(S.epart.p, 0, S.epart.bytes, stream_));
     D.epart = (double *)S.epart.p;
+    D.end_g = end_slices(S.ntiles, c.n_species, S.ybx * S.yby);
     S.hist_cap = c.energy_every > 0 ? 4096 : 1;
     if (!dalloc(S.hist, sizeof(zpic_energy_rec) * S.hist_cap))
       return fail(ZPIC_ENOMEM, "history");
@@ -1364,12 +1365,14 @@ class Batch : public BatchBase {
     std::vector<std::pair<long long, int2>> load;
     int yee_n = 0;
     max_tx_ = max_ty_ = 2;
+    end_g_max_ = 1;
     all16_ = true;
     for (int i = 0; i < n_sims; ++i) {
       SimHost<R> &S = sims_[i];
       max_tx_ = std::max(max_tx_, S.tx);
       max_ty_ = std::max(max_ty_, S.ty);
       all16_ = all16_ && S.tx == 16 && S.ty == 16;
+      end_g_max_ = std::max(end_g_max_, S.dev.end_g);
       for (int t = 0; t < S.ntiles; ++t) {
         long long l = 0;
         for (auto &P : S.sp) l += P.h_cnt.empty() ? 0 : P.h_cnt[t];
@@ -1657,7 +1660,7 @@ class Batch : public BatchBase {
         return launch_migrate<R>(dsims(), (const int2 *)items_.p, n_items_,
                                  dst(), ovf_, stream_);
       case 3:
-        return launch_end_step<R>(dsims(), n_sims, dst(), stream_);
+        return launch_end_step<R>(dsims(), n_sims, end_g_max_, dst(), stream_);
       case 5:
         return launch_sort_tiles<R>(dsims(), n_sims, (const int2 *)items_.p,
                                     n_items_, dst(), stream_);
@@ -1800,6 +1803,7 @@ class Batch : public BatchBase {
   int ovf_cap_ = 0;
   int n_items_ = 0, n_yee_ = 0, max_tx_ = 2, max_ty_ = 2;
   bool all16_ = false;
+  int end_g_max_ = 1;  // most end-of-step slices of a member
   BatchStatus *h_st_ = nullptr;
   std::vector<SimDev<R>> uploaded_;  // descriptors as last uploaded
   long long target_ = 0;

@@ -31,9 +31,20 @@ namespace zp {
 constexpr int kMaxSpecies = ZPIC_MAX_SPECIES;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-// Most CTAs that share the end-of-step energy reduction of one simulation
-// (each sums a slice of the partials; the last one to finish combines them).
-constexpr int kEndSlices = 16;
+// CTAs that share the end-of-step energy reduction of one simulation (each
+// sums a slice of the partials; the last one to finish combines them): one
+// per 640 partial values, at most kEndSlicesMax.  The FP64 sums run on the
+// GPU's few FP64 units, so a large grid spreads them over many SMs (64
+// slices for a 2048^2 grid: 0.037 ms per step, 0.041 ms with 16), a small
+// one keeps the fixed cost of each slice's reduction tree low (the
+// 256-simulation batch: 0.008 ms, 0.016 ms with 16 slices each).  The count depends on
+// the simulation alone, so it gives the same bits in a batch and alone.
+constexpr int kEndSlicesMax = 64;
+__host__ __device__ inline int end_slices(int ntiles, int nsp, int nyb) {
+  const long long parts = (long long)ntiles * nsp + 2LL * nyb;
+  const long long g = (parts + 639) / 640;
+  return (int)(g < 1 ? 1 : (g > kEndSlicesMax ? kEndSlicesMax : g));
+}
 // Values of one slice: kinetic energy per species, E^2, B^2.
 constexpr int kEndQ = kMaxSpecies + 2;
 
@@ -124,9 +135,10 @@ struct SimDev {
   double jscale_d[3];
   double *part_kin;            // [kMaxSpecies][ntiles] kinetic partials
   double *part_fld;            // [ybx*yby][2] field-energy partials
-  double *epart;               // [kEndSlices][kEndQ][2] compensated sums
+  double *epart;               // [end_g][kEndQ][2] compensated sums
                                // (sum, error) of the end-of-step slices
   int *eticket;                // slices of this simulation finished
+  int end_g;                   // end-of-step slices of this simulation
   zpic_energy_rec *hist;       // energy history
   int hist_cap;
   int hist_skip;               // records before the first one kept (a run

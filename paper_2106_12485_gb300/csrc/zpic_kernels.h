@@ -75,7 +75,7 @@ cudaError_t launch_sort_tiles(const SimDev<R> *sims, int n_sims,
 
 // Energy records, window counter, step counter.
 template <typename R>
-cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims,
+cudaError_t launch_end_step(const SimDev<R> *sims, int n_sims, int g_max,
                             BatchStatus *st, cudaStream_t stream);
 
 // Device pointers of the six field components (row length ld).
