@@ -277,7 +277,9 @@ __device__ __forceinline__ void queue_put(const SegQueue<R> &q, int slot,
   q.cell[slot] = (lx + 1) | ((ly + 1) << 8);
 }
 
-template <typename R>
+// kWhole: the start-cell segment was not deposited in the particle loop
+// either (see kWholeQueue), so it is deposited here with the others.
+template <typename R, bool kWhole>
 __device__ __forceinline__ void queue_take(const SegQueue<R> &q,
                                            const TileJ<R> &J, int JW, int JP,
                                            int slot, R qx0, R qy0) {
@@ -288,6 +290,9 @@ __device__ __forceinline__ void queue_take(const SegQueue<R> &q,
   const PathSplit<R> p =
       split_path(x, y, q.v[2 * kQ + slot], q.v[3 * kQ + slot]);
   const R qx = qx0 * w, qy = qy0 * w;
+  if (kWhole)  // segment 1: from the start to the first crossing point
+    dep_seg(J, JW, JP, lx, ly, x, y, p.xfirst ? p.xb : p.x_sy,
+            p.xfirst ? p.x_sx_y : p.yb, p.s1, qx, qy, qz);
   // segment 2: from the first crossing point into the cell entered there
   const int c2x = p.xfirst ? p.di : 0, c2y = p.xfirst ? 0 : p.dj;
   const R ax2 = p.xfirst ? p.xb - R(p.di) : p.x_sy;
@@ -627,6 +632,13 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   // which neighbouring slots hold neighbouring cells keeps that order from
   // step to step, and so do its bank-conflict-free gathers and deposits.
   constexpr int kS = Ring<R>::kStages;
+  // FP64: the split of a crossing path (two divisions, a dozen compares)
+  // and all its segments are left to the queue, which takes 32 crossing
+  // paths at a time, so the particle loop spends no FP64 work on them (the
+  // FP64 form is bound by the FP64 unit).  FP32 splits in the loop: it is
+  // bound by issue and shared memory, and the queue would then deposit the
+  // start-cell segment as extra atomics.
+  constexpr bool kWholeQueue = sizeof(R) == 8;
   const int NC = (n + 31) >> 5;
   const int ca = warp * NC / kPW, cb = (warp + 1) * NC / kPW;
   const int nch = cb - ca;
@@ -736,11 +748,25 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
     if (T.do_energy) kin += wd * u2 * fdiv<R>(rgn, R(1) + rgn);
     const R x1 = x + T.dt_dx * ux * rgn;
     const R y1 = y + T.dt_dy * uy * rgn;
-    const PathSplit<R> ps = split_path(x, y, x1, y1);
+    PathSplit<R> ps;
+    if constexpr (kWholeQueue) {
+      // the cell steps and stored offsets only; the split of a crossing
+      // path waits for the queue
+      R xe = x1, ye = y1;
+      ps.di = axis_cross(xe, ps.xf);
+      ps.dj = axis_cross(ye, ps.yf);
+      ps.cut = (ps.di | ps.dj) != 0;
+    } else {
+      ps = split_path(x, y, x1, y1);
+    }
 
     // ---- stage 3: charge-conserving deposit, segment in the start cell ----
     const R qz = q00 * wd * uz * rgn;
-    {
+    if constexpr (kWholeQueue) {
+      if (!ps.cut)  // a path inside its cell
+        dep_seg(T.jt, JW, JP, lx, ly, x, y, ps.xf, ps.yf, R(1), qx0 * wd,
+                qy0 * wd, qz);
+    } else {
       const R bx1 = ps.cut ? (ps.xfirst ? ps.xb : ps.x_sy) : ps.xf;
       const R by1 = ps.cut ? (ps.xfirst ? ps.x_sx_y : ps.yb) : ps.yf;
       dep_seg(T.jt, JW, JP, lx, ly, x, y, bx1, by1, ps.s1, qx0 * wd,
@@ -758,7 +784,8 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
       // a put adds at most 32, and a full run of 32 is drained at once
       __syncwarp();
       if (qtail - qhead >= 32) {
-        queue_take(T.q, T.jt, JW, JP, (qhead + lane) & (kQ - 1), qx0, qy0);
+        queue_take<R, kWholeQueue>(T.q, T.jt, JW, JP,
+                                   (qhead + lane) & (kQ - 1), qx0, qy0);
         qhead += 32;
         __syncwarp();
       }
@@ -819,7 +846,8 @@ __device__ __forceinline__ void push_species(const SimDev<R> &S, const int s,
   // segments still waiting in the warp's queue
   __syncwarp();
   if (lane < qtail - qhead)
-    queue_take(T.q, T.jt, JW, JP, (qhead + lane) & (kQ - 1), qx0, qy0);
+    queue_take<R, kWholeQueue>(T.q, T.jt, JW, JP,
+                               (qhead + lane) & (kQ - 1), qx0, qy0);
   if (lane == 0) T.s_stay[warp] = n_stay;
   if (n_removed) atomicAdd(&S.removed[s], n_removed);
   if (T.do_energy)
