@@ -482,7 +482,12 @@ int zpic_profile_read(zpic_sim *sim, char *names, size_t name_len,
  * configurations (ZPIC_EINVAL if they differ in precision); zpic_batch_step
  * and zpic_batch_sync behave like zpic_step and zpic_sync for all members;
  * zpic_batch_sim gives a view handle for the getters (views are freed with
- * the batch; zpic_destroy on a view is ZPIC_EINVAL). */
+ * the batch; zpic_destroy on a view is ZPIC_EINVAL).  With n >= 2, members
+ * that leave the tile size, re-sort interval or CTAs per SM at 0 take the
+ * choice of zpic_batch_autotune for this list of configuration classes if
+ * it has run, else a 16 x 16 tile (not the per-class choice of
+ * zpic_autotune, made for one simulation alone on the GPU); with n = 1 the
+ * rules of zpic_create apply. */
 int zpic_batch_create(const zpic_config *cfgs, int n, zpic_batch **out);
 int zpic_batch_step(zpic_batch *b, int n);
 int zpic_batch_sync(zpic_batch *b);
