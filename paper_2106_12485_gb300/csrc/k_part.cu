@@ -347,32 +347,127 @@ cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
 // its 32-cell words; a particle of cell c that takes rank r (in the order
 // the slots are read) goes to slot T(r) + (cells before c that hold more
 // than r particles), T(r) being the number of particles of rank below r.
-// Ranks are handed out chunk by chunk of slots (a barrier between chunks),
-// so a store that is already close to that order (the particle kernel keeps
-// it between re-sorts) is rewritten in long contiguous runs.  A tile whose
-// rank table exceeds the shared-memory budget keeps its order.
-constexpr int kSortThreads = 256;
+// A species of a tile with at most kSortStaged<R> particles is moved plane
+// by plane through shared memory: its cells and the permutation (which
+// input slot each output slot takes) stay there, each plane arrives by one
+// bulk asynchronous copy (the first one while the rank tables are built)
+// and is written out in slot order, so every global access is coalesced
+// whatever the permutation.  The particles of one cell then take their
+// ranks in any order.  Larger ones are moved particle by particle, kSortU
+// chunks of slots per memory round trip, the chunks taking their ranks one
+// after the other so that a store close to the sorted order is rewritten in
+// long runs.  A tile whose rank table exceeds the shared-memory budget keeps
+// its order.
+constexpr int kSortThreads = 512;
 constexpr int kSortMaxCells = 1024;   // tiles up to 32 x 32
 constexpr int kSortMaskWords = 6144;  // ranks x 32-cell words
 constexpr int kSortMaxRank = 2048;
 constexpr int kSortU = 4;             // chunks of slots per memory round trip
+// particles of one species and tile that the staged path takes
+template <typename R>
+constexpr int kSortStaged = sizeof(R) == 4 ? 20480 : 13312;
 
+__host__ __device__ constexpr size_t sort_tables_bytes() {
+  return ((2 * (size_t)kSortMaskWords + kSortMaxRank + 1) * sizeof(unsigned) +
+          15) & ~size_t(15);
+}
+template <typename R>
 size_t sort_smem_bytes() {
-  return (2 * (size_t)kSortMaskWords + kSortMaxRank + 1) * sizeof(unsigned);
+  // tables, then cells and permutation (16-bit slots), then one plane
+  return sort_tables_bytes() + 4 * (size_t)kSortStaged<R> +
+         sizeof(R) * (size_t)kSortStaged<R>;
+}
+
+// Bulk asynchronous copies into shared memory, completed on an mbarrier.
+// Addresses are 16-byte aligned (segments start at multiples of 32
+// particles, planes at 256-byte boundaries) and sizes multiples of 16.
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb))
+               : "memory");
+}
+// the calling thread's arrival, expecting `bytes`, then the copy (if any)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src,
+                                          unsigned bytes,
+                                          unsigned long long *mb) {
+  // shared memory that threads have read is written by the async proxy next
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_addr(mb)),
+      "r"(bytes)
+      : "memory");
+  if (bytes)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mb))
+        : "memory");
+}
+// Wait for phase `parity` of mb to complete; false if it did not within
+// the iteration limit.
+constexpr int kBulkWaitLimit = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mb,
+                                          unsigned parity) {
+  const unsigned a = smem_addr(mb);
+  for (int i = 0; i < kBulkWaitLimit; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred q;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Plane k of a species' copy (x, y, ux, uy, uz, then w and id if present):
+// its address and element size.
+template <typename R>
+__device__ __forceinline__ int sort_plane_ptr(const Planes<R> &P, int k,
+                                              const void *&src) {
+  const R *r[5] = {P.x, P.y, P.ux, P.uy, P.uz};
+  if (k < 5) { src = r[k]; return (int)sizeof(R); }
+  if (k == 5 && P.w) { src = P.w; return (int)sizeof(R); }
+  src = P.id;
+  return 4;
+}
+
+// dst[d] = buf[pinv[d]] for every output slot d of a plane
+template <typename T>
+__device__ __forceinline__ void sort_gather(T *__restrict__ dst,
+                                            const T *buf,
+                                            const uint16_t *pinv, int n) {
+#pragma unroll 4
+  for (int d = threadIdx.x; d < n; d += blockDim.x)
+    __stcs(dst + d, buf[pinv[d]]);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kSortThreads, 3)
+__global__ void __launch_bounds__(kSortThreads, 1)
     sort_tiles_kernel(const SimDev<R> *__restrict__ sims,
                       int n_sims, const int2 *__restrict__ items,
                       int n_items, BatchStatus *st) {
   __shared__ int hist[kSortMaxCells];  // cell counts, then rank cursors
   __shared__ int wsum[kSortThreads / 32];
   __shared__ int s_max;
-  extern __shared__ unsigned sort_smem[];
+  extern __shared__ __align__(16) unsigned sort_smem[];
   unsigned *mask = sort_smem;
   unsigned *pre = sort_smem + kSortMaskWords;
   int *T = reinterpret_cast<int *>(sort_smem + 2 * kSortMaskWords);
+  constexpr int NS = kSortStaged<R>;
+  unsigned char *stage =
+      reinterpret_cast<unsigned char *>(sort_smem) + sort_tables_bytes();
+  uint16_t *cells_s = reinterpret_cast<uint16_t *>(stage);
+  uint16_t *pinv = cells_s + NS;
+  unsigned char *buf = stage + 4 * (size_t)NS;
+  __shared__ unsigned long long mb_cell, mb_plane;
+  unsigned ph_cell = 0, ph_plane = 0;
   const int step = st->step;
   if (frozen(st, step)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -384,6 +479,25 @@ __global__ void __launch_bounds__(kSortThreads, 3)
       due = sort_due(sims[i], step);
     if (!__syncthreads_or(due)) return;
   }
+  if (threadIdx.x == 0) {
+    mbar_init(&mb_cell);
+    mbar_init(&mb_plane);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // a copy that did not complete: record it, give the copies in flight one
+  // more bounded wait, and leave (every thread takes the same decision)
+  // (the cell copy's phase, if it is the one in question, then the plane's)
+  auto gave_up = [&](bool ok, bool cell, unsigned ph_c, unsigned ph_p) {
+    if (!__syncthreads_or(!ok)) return false;
+    if (threadIdx.x == 0) {
+      atomicOr(&st->error, ERR_TIMEOUT);
+      atomicMin(&st->err_step, step);
+      if (cell) mbar_wait(&mb_cell, ph_c);
+      mbar_wait(&mb_plane, ph_p);
+    }
+    return true;
+  };
   for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
     const int2 it = items[ii];
     const SimDev<R> &S = sims[it.x];
@@ -405,10 +519,33 @@ __global__ void __launch_bounds__(kSortThreads, 3)
       for (int c = threadIdx.x; c < nc; c += blockDim.x) hist[c] = 0;
       if (threadIdx.x == 0) s_max = 0;
       __syncthreads();
+      const bool staged = n <= NS;
+      const int np = 5 + (I.w ? 1 : 0) + (I.id ? 1 : 0);
+      if (staged) {
+        // the cells, and the first plane while the tables are built
+        if (threadIdx.x == 0) {
+          const void *src;
+          const int es = sort_plane_ptr(I, 0, src);
+          bulk_load(cells_s, I.cell + base, (unsigned)(n & ~7) * 2u, &mb_cell);
+          bulk_load(buf, (const char *)src + base * es,
+                    (unsigned)(n & ~(16 / es - 1)) * es, &mb_plane);
+        }
+        for (int p = (n & ~7) + threadIdx.x; p < n; p += blockDim.x)
+          cells_s[p] = I.cell[base + p];
+        const bool ok = mbar_wait(&mb_cell, ph_cell);
+        ph_cell ^= 1u;
+        if (gave_up(ok, true, ph_cell ^ 1u, ph_plane)) return;
 #pragma unroll 4
-      for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const int lc = I.cell[base + p];
-        atomicAdd(&hist[(lc >> 8) * tw + (lc & 255)], 1);
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          const int lc = cells_s[p];
+          atomicAdd(&hist[(lc >> 8) * tw + (lc & 255)], 1);
+        }
+      } else {
+#pragma unroll 4
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          const int lc = I.cell[base + p];
+          atomicAdd(&hist[(lc >> 8) * tw + (lc & 255)], 1);
+        }
       }
       __syncthreads();
       int m = 0;
@@ -456,6 +593,65 @@ __global__ void __launch_bounds__(kSortThreads, 3)
       }
       for (int c = threadIdx.x; c < nc; c += blockDim.x) hist[c] = 0;
       __syncthreads();
+      if (staged && !fits) {
+        // the first plane's copy is not used: let it land before the
+        // particle-by-particle path
+        const bool ok = mbar_wait(&mb_plane, ph_plane);
+        ph_plane ^= 1u;
+        if (gave_up(ok, false, 0u, ph_plane ^ 1u)) return;
+      }
+      if (fits && staged) {
+        // output slot d takes input slot pinv[d]
+#pragma unroll 4
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          const int lc = cells_s[p];
+          const int li = (lc >> 8) * tw + (lc & 255);
+          const int r = atomicAdd(&hist[li], 1);
+          const int wd = r * W + (li >> 5);
+          const int d = T[r] + (int)pre[wd] +
+                        __popc(mask[wd] & ((1u << (li & 31)) - 1u));
+          pinv[d] = (uint16_t)p;
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < n; d += blockDim.x)
+          O.cell[base + d] = cells_s[pinv[d]];
+        for (int k = 0; k < np; ++k) {
+          const void *src;
+          const int es = sort_plane_ptr(I, k, src);
+          const char *sp = (const char *)src + base * es;
+          const void *dsrc;
+          sort_plane_ptr(O, k, dsrc);
+          char *dp = (char *)dsrc + base * es;
+          // the ragged end of the plane with plain loads
+          for (int p = (n & ~(16 / es - 1)) + threadIdx.x; p < n;
+               p += blockDim.x) {
+            if (es == 8)
+              reinterpret_cast<unsigned long long *>(buf)[p] =
+                  reinterpret_cast<const unsigned long long *>(sp)[p];
+            else
+              reinterpret_cast<unsigned *>(buf)[p] =
+                  reinterpret_cast<const unsigned *>(sp)[p];
+          }
+          const bool ok = mbar_wait(&mb_plane, ph_plane);
+          ph_plane ^= 1u;
+          if (gave_up(ok, false, 0u, ph_plane ^ 1u)) return;
+          if (es == 8)
+            sort_gather(reinterpret_cast<unsigned long long *>(dp),
+                        reinterpret_cast<const unsigned long long *>(buf),
+                        pinv, n);
+          else
+            sort_gather(reinterpret_cast<unsigned *>(dp),
+                        reinterpret_cast<const unsigned *>(buf), pinv, n);
+          __syncthreads();  // buf is read: the next plane may land
+          if (threadIdx.x == 0 && k + 1 < np) {
+            const void *nsrc;
+            const int nes = sort_plane_ptr(I, k + 1, nsrc);
+            bulk_load(buf, (const char *)nsrc + base * nes,
+                      (unsigned)(n & ~(16 / nes - 1)) * nes, &mb_plane);
+          }
+        }
+        continue;
+      }
       // kSortU chunks of slots per round trip: every thread loads its
       // particle of each chunk first, then the chunks take their ranks one
       // after the other
@@ -512,7 +708,7 @@ template <typename R>
 cudaError_t prepare_sort_tiles() {
   return cudaFuncSetAttribute(sort_tiles_kernel<R>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sort_smem_bytes());
+                              (int)sort_smem_bytes<R>());
 }
 
 template <typename R>
@@ -525,8 +721,8 @@ cudaError_t launch_sort_tiles(const SimDev<R> *sims, int n_sims,
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
           cudaSuccess)
     sms = 148;
-  const int grid = n_items < 3 * sms ? n_items : 3 * sms;
-  sort_tiles_kernel<R><<<grid, kSortThreads, sort_smem_bytes(), stream>>>(
+  const int grid = n_items < sms ? n_items : sms;
+  sort_tiles_kernel<R><<<grid, kSortThreads, sort_smem_bytes<R>(), stream>>>(
       sims, n_sims, items, n_items, st);
   return cudaGetLastError();
 }

@@ -54,7 +54,8 @@ constexpr int ERR_LOST = 2;      // overflow buffer full: particles dropped
 constexpr int ERR_NAN = 4;       // non-finite energy
 constexpr int ERR_STORE = 8;     // a stored particle lies outside its tile
 constexpr int ERR_TIMEOUT = 16;  // a bounded device wait gave up (reported as
-                                 // ZPIC_ETIMEOUT; no current kernel spins)
+                                 // ZPIC_ETIMEOUT): the re-sort's wait for a
+                                 // bulk copy into shared memory
 
 struct BatchStatus {
   int step;         // completed steps

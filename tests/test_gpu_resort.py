@@ -138,3 +138,42 @@ def test_autotune_all_chooses_and_create_uses_it():
     sim2 = Z.Sim(W.uniform_thermal(256, 256, ppc=(4, 4), sort_every=7,
                                    push_ctas_per_sm=1))
     assert sim2.info().sort_every == 7 and sim2.info().push_ctas_per_sm == 1
+
+
+@pytest.mark.parametrize("tile,ppc,prec", [
+    ((16, 16), (4, 4), Z.FP32),   # through shared memory
+    ((32, 32), (5, 5), Z.FP32),   # 25,600 particles a tile: slot by slot
+    ((16, 16), (4, 4), Z.FP64),   # through shared memory
+    ((16, 16), (8, 8), Z.FP64),   # 16,384 > the FP64 staging room
+])
+def test_resort_order_and_whole_records(tile, ppc, prec):
+    # both ways of moving a tile's particles give the cell-interleaved order
+    # and move every record whole (compared by id with a run that does not
+    # re-sort; the FP64 deposit is made order-independent for this)
+    nx = ny = 64
+    det = prec == Z.FP64
+
+    def make(every):
+        return Z.Sim(W.uniform_thermal(nx, ny, ppc=ppc, tile=tile,
+                                       precision=prec, track_ids=True,
+                                       deterministic=det, sort_every=every))
+    a, b = make(-1), make(2)
+    a.step(2)
+    b.step(2)
+    assert b.info().sorts == 1 and a.info().sorts == 0
+    ntx = nx // tile[0]
+    cnt = b.tile_counts(0)
+    for t in (0, ntx + 1):
+        st = b.particles(0, tiles=(t, t + 1))
+        tx0, ty0 = (t % ntx) * tile[0], (t // ntx) * tile[1]
+        lc = (st["iy"] - ty0) * tile[0] + (st["ix"] - tx0)
+        assert len(lc) == cnt[t]
+        counts = np.bincount(lc, minlength=tile[0] * tile[1])
+        want = np.concatenate([np.nonzero(counts > r)[0]
+                               for r in range(counts.max())])
+        np.testing.assert_array_equal(lc, want)
+    pa, pb = a.particles(0), b.particles(0)
+    oa = np.argsort(pa["id"], kind="stable")
+    ob = np.argsort(pb["id"], kind="stable")
+    for k in pa:
+        np.testing.assert_array_equal(pa[k][oa], pb[k][ob], err_msg=k)
