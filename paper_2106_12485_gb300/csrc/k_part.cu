@@ -350,9 +350,11 @@ cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
 // A species of a tile with at most kSortStaged<R> particles is moved plane
 // by plane through shared memory: its cells and the permutation (which
 // input slot each output slot takes) stay there, each plane arrives by one
-// bulk asynchronous copy (the first one while the rank tables are built)
-// and is written out in slot order, so every global access is coalesced
-// whatever the permutation.  The particles of one cell then take their
+// bulk asynchronous copy and is written out in slot order, so every global
+// access is coalesced whatever the permutation.  The first plane's copy
+// runs while the rank tables are built, and each later one while the plane
+// before it is written out (into a second buffer laid over the tables and
+// the cells, when a plane fits there: always in FP32).  The particles of one cell then take their
 // ranks in any order.  Larger ones are moved particle by particle, kSortU
 // chunks of slots per memory round trip, the chunks taking their ranks one
 // after the other so that a store close to the sorted order is rewritten in
@@ -431,11 +433,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *mb,
 template <typename R>
 __device__ __forceinline__ int sort_plane_ptr(const Planes<R> &P, int k,
                                               const void *&src) {
-  const R *r[5] = {P.x, P.y, P.ux, P.uy, P.uz};
-  if (k < 5) { src = r[k]; return (int)sizeof(R); }
-  if (k == 5 && P.w) { src = P.w; return (int)sizeof(R); }
-  src = P.id;
-  return 4;
+  switch (k) {
+    case 0: src = P.x; return (int)sizeof(R);
+    case 1: src = P.y; return (int)sizeof(R);
+    case 2: src = P.ux; return (int)sizeof(R);
+    case 3: src = P.uy; return (int)sizeof(R);
+    case 4: src = P.uz; return (int)sizeof(R);
+    default:
+      if (k == 5 && P.w) { src = P.w; return (int)sizeof(R); }
+      src = P.id;
+      return 4;
+  }
 }
 
 // dst[d] = buf[pinv[d]] for every output slot d of a plane
@@ -465,9 +473,15 @@ __global__ void __launch_bounds__(kSortThreads, 1)
       reinterpret_cast<unsigned char *>(sort_smem) + sort_tables_bytes();
   uint16_t *cells_s = reinterpret_cast<uint16_t *>(stage);
   uint16_t *pinv = cells_s + NS;
-  unsigned char *buf = stage + 4 * (size_t)NS;
-  __shared__ unsigned long long mb_cell, mb_plane;
-  unsigned ph_cell = 0, ph_plane = 0;
+  // plane buffers: buf0 after the permutation; buf1 over the tables and
+  // the cells, which are no longer needed once the permutation is built
+  unsigned char *const buf0 = stage + 4 * (size_t)NS;
+  unsigned char *const buf1 = reinterpret_cast<unsigned char *>(sort_smem);
+  constexpr size_t kBuf1Bytes = sort_tables_bytes() + 2 * (size_t)NS;
+  // mbarriers: the cell copy, then one per plane buffer; ph bit i = the
+  // parity of mb[i]'s next phase, pend bit i = a copy on mb[i] not waited for
+  __shared__ unsigned long long mb[3];
+  unsigned ph = 0, pend = 0;
   const int step = st->step;
   if (frozen(st, step)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -480,23 +494,44 @@ __global__ void __launch_bounds__(kSortThreads, 1)
     if (!__syncthreads_or(due)) return;
   }
   if (threadIdx.x == 0) {
-    mbar_init(&mb_cell);
-    mbar_init(&mb_plane);
+    for (int i = 0; i < 3; ++i) mbar_init(&mb[i]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // a copy that did not complete: record it, give the copies in flight one
-  // more bounded wait, and leave (every thread takes the same decision)
-  // (the cell copy's phase, if it is the one in question, then the plane's)
-  auto gave_up = [&](bool ok, bool cell, unsigned ph_c, unsigned ph_p) {
-    if (!__syncthreads_or(!ok)) return false;
-    if (threadIdx.x == 0) {
-      atomicOr(&st->error, ERR_TIMEOUT);
-      atomicMin(&st->err_step, step);
-      if (cell) mbar_wait(&mb_cell, ph_c);
-      mbar_wait(&mb_plane, ph_p);
+  // copy `bytes` from src into dst on mb[i] (thread 0 issues it; every
+  // thread records it)
+  auto start_copy = [&](int i, void *dst, const void *src, unsigned bytes) {
+    if (threadIdx.x == 0) bulk_load(dst, src, bytes, &mb[i]);
+    pend |= 1u << i;
+  };
+  // wait for the copy on mb[i] and make it (and every thread's plain stores
+  // before the call) visible to the CTA.  A copy that does not complete
+  // in time is recorded, the copies in flight get one more bounded wait,
+  // and every thread leaves (false).
+  auto finish_copy = [&](int i) {
+    const bool ok = mbar_wait(&mb[i], (ph >> i) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&st->error, ERR_TIMEOUT);
+        atomicMin(&st->err_step, step);
+        for (int j = 0; j < 3; ++j)
+          if ((pend >> j) & 1u) mbar_wait(&mb[j], (ph >> j) & 1u);
+      }
+      return false;
     }
+    ph ^= 1u << i;
+    pend &= ~(1u << i);
     return true;
+  };
+  // plane k of a copy of the store at the segment start, its element size,
+  // and the bytes of its 16-byte multiple that a bulk copy takes
+  auto plane_at = [&](const Planes<R> &Q, int k, size_t base, int n,
+                      const char *&ptr, unsigned &bulk) {
+    const void *p0;
+    const int es = sort_plane_ptr(Q, k, p0);
+    ptr = (const char *)p0 + base * es;
+    bulk = (unsigned)(n & ~(16 / es - 1)) * es;
+    return es;
   };
   for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
     const int2 it = items[ii];
@@ -521,20 +556,18 @@ __global__ void __launch_bounds__(kSortThreads, 1)
       __syncthreads();
       const bool staged = n <= NS;
       const int np = 5 + (I.w ? 1 : 0) + (I.id ? 1 : 0);
+      // two plane buffers when a plane fits over the tables and the cells
+      const bool dbl = (size_t)n * sizeof(R) <= kBuf1Bytes;
       if (staged) {
         // the cells, and the first plane while the tables are built
-        if (threadIdx.x == 0) {
-          const void *src;
-          const int es = sort_plane_ptr(I, 0, src);
-          bulk_load(cells_s, I.cell + base, (unsigned)(n & ~7) * 2u, &mb_cell);
-          bulk_load(buf, (const char *)src + base * es,
-                    (unsigned)(n & ~(16 / es - 1)) * es, &mb_plane);
-        }
+        const char *p0;
+        unsigned b0;
+        plane_at(I, 0, base, n, p0, b0);
+        start_copy(0, cells_s, I.cell + base, (unsigned)(n & ~7) * 2u);
+        start_copy(1, buf0, p0, b0);
         for (int p = (n & ~7) + threadIdx.x; p < n; p += blockDim.x)
           cells_s[p] = I.cell[base + p];
-        const bool ok = mbar_wait(&mb_cell, ph_cell);
-        ph_cell ^= 1u;
-        if (gave_up(ok, true, ph_cell ^ 1u, ph_plane)) return;
+        if (!finish_copy(0)) return;
 #pragma unroll 4
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
           const int lc = cells_s[p];
@@ -596,9 +629,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
       if (staged && !fits) {
         // the first plane's copy is not used: let it land before the
         // particle-by-particle path
-        const bool ok = mbar_wait(&mb_plane, ph_plane);
-        ph_plane ^= 1u;
-        if (gave_up(ok, false, 0u, ph_plane ^ 1u)) return;
+        if (!finish_copy(1)) return;
       }
       if (fits && staged) {
         // output slot d takes input slot pinv[d]
@@ -615,39 +646,49 @@ __global__ void __launch_bounds__(kSortThreads, 1)
         __syncthreads();
         for (int d = threadIdx.x; d < n; d += blockDim.x)
           O.cell[base + d] = cells_s[pinv[d]];
+        const int nb = dbl ? 2 : 1;
+        if (dbl && np > 1) {
+          __syncthreads();  // the tables and the cells are read
+          const char *p1;
+          unsigned b1;
+          plane_at(I, 1, base, n, p1, b1);
+          start_copy(2, buf1, p1, b1);
+        }
+        // plane k lands in buf0 (k even, or one buffer) or buf1; while it is
+        // written out, plane k + 1 is on its way into the other one
         for (int k = 0; k < np; ++k) {
-          const void *src;
-          const int es = sort_plane_ptr(I, k, src);
-          const char *sp = (const char *)src + base * es;
-          const void *dsrc;
-          sort_plane_ptr(O, k, dsrc);
-          char *dp = (char *)dsrc + base * es;
+          const int b = nb == 2 ? (k & 1) : 0;
+          unsigned char *bk = b ? buf1 : buf0;
+          const char *sp;
+          unsigned bulk;
+          const int es = plane_at(I, k, base, n, sp, bulk);
+          const char *dq;
+          unsigned dbulk;
+          plane_at(O, k, base, n, dq, dbulk);
+          char *dp = const_cast<char *>(dq);
           // the ragged end of the plane with plain loads
-          for (int p = (n & ~(16 / es - 1)) + threadIdx.x; p < n;
-               p += blockDim.x) {
+          for (int p = (int)(bulk / es) + threadIdx.x; p < n; p += blockDim.x) {
             if (es == 8)
-              reinterpret_cast<unsigned long long *>(buf)[p] =
+              reinterpret_cast<unsigned long long *>(bk)[p] =
                   reinterpret_cast<const unsigned long long *>(sp)[p];
             else
-              reinterpret_cast<unsigned *>(buf)[p] =
+              reinterpret_cast<unsigned *>(bk)[p] =
                   reinterpret_cast<const unsigned *>(sp)[p];
           }
-          const bool ok = mbar_wait(&mb_plane, ph_plane);
-          ph_plane ^= 1u;
-          if (gave_up(ok, false, 0u, ph_plane ^ 1u)) return;
+          if (!finish_copy(1 + b)) return;
           if (es == 8)
             sort_gather(reinterpret_cast<unsigned long long *>(dp),
-                        reinterpret_cast<const unsigned long long *>(buf),
+                        reinterpret_cast<const unsigned long long *>(bk),
                         pinv, n);
           else
             sort_gather(reinterpret_cast<unsigned *>(dp),
-                        reinterpret_cast<const unsigned *>(buf), pinv, n);
-          __syncthreads();  // buf is read: the next plane may land
-          if (threadIdx.x == 0 && k + 1 < np) {
-            const void *nsrc;
-            const int nes = sort_plane_ptr(I, k + 1, nsrc);
-            bulk_load(buf, (const char *)nsrc + base * nes,
-                      (unsigned)(n & ~(16 / nes - 1)) * nes, &mb_plane);
+                        reinterpret_cast<const unsigned *>(bk), pinv, n);
+          __syncthreads();  // bk is read: plane k + nb may land there
+          if (k + nb < np) {
+            const char *pn;
+            unsigned bn;
+            plane_at(I, k + nb, base, n, pn, bn);
+            start_copy(1 + b, bk, pn, bn);
           }
         }
         continue;

@@ -143,7 +143,8 @@ def test_autotune_all_chooses_and_create_uses_it():
 @pytest.mark.parametrize("tile,ppc,prec", [
     ((16, 16), (4, 4), Z.FP32),   # through shared memory
     ((32, 32), (5, 5), Z.FP32),   # 25,600 particles a tile: slot by slot
-    ((16, 16), (4, 4), Z.FP64),   # through shared memory
+    ((16, 16), (4, 4), Z.FP64),   # through shared memory, two plane buffers
+    ((16, 16), (7, 7), Z.FP64),   # 12,544 particles a tile: one plane buffer
     ((16, 16), (8, 8), Z.FP64),   # 16,384 > the FP64 staging room
 ])
 def test_resort_order_and_whole_records(tile, ppc, prec):
