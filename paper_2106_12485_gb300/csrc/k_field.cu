@@ -167,8 +167,29 @@ __device__ __forceinline__ void block_sum2_store(R e, R b, double *red,
   }
 }
 
+// resident Yee CTAs per SM the register budget is sized for (64 registers
+// in FP32; on a 2048^2 grid 0.102 ms per step, 0.104 ms at 3 CTAs per SM and
+// 0.125 ms at 5, compiled for 48 registers)
+constexpr int kYeeCtas = 4;
+
+// Asynchronous copy of one field value (4 or 8 bytes) into shared memory;
+// nbytes = 0 writes a zero instead of reading.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 3)
+__device__ __forceinline__ void cp_async_val(R *dst, const R *src,
+                                             unsigned nbytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(R) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d),
+                 "l"(src), "r"(nbytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d),
+                 "l"(src), "r"(nbytes)
+                 : "memory");
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, kYeeCtas)
     yee_kernel(const SimDev<R> *__restrict__ sims,
                const int2 *__restrict__ items, BatchStatus *st) {
   constexpr int X = kYeeX, Y = yee_rows<R>();
@@ -199,8 +220,10 @@ __global__ void __launch_bounds__(kThreads, 3)
   // The block's halo, cells [x0-1, x0+X+2) x [y0-1, y0+Y+2): E uses all of
   // it, B the first BW x BH, J the part from (x0, y0) on.  Each thread takes
   // halo cells k = tid + u kThreads, works out the cell's address once for
-  // all nine arrays, and issues every load before its first shared-memory
-  // store, so a block waits for one memory round trip.
+  // all nine arrays, and issues every load before it waits, so a block
+  // waits for one memory round trip: E and B go straight into shared memory
+  // by asynchronous copies (no registers held), J through registers (it is
+  // scaled on the way in).
   constexpr int HN = EH * EW;
   constexpr int UH = (HN + kThreads - 1) / kThreads;
   const bool filtered = S.Jf[0] != nullptr;  // drive E with the filtered J
@@ -224,16 +247,16 @@ __global__ void __launch_bounds__(kThreads, 3)
     off[u] = (size_t)gj * S.ld + (ok ? gi : 0);
     hl[u] = (lj << 8) | li;
   }
-  R ve[3][UH], vb[3][UH];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R *__restrict__ pe = S.E[cur][c];
-    const R *__restrict__ pb = S.B[cur][c];
+  for (int u = 0; u < UH; ++u) {
+    if (threadIdx.x + u * kThreads >= HN) continue;
+    const int lj = hl[u] >> 8, li = hl[u] & 255;
+    const unsigned nb = in[u] ? (unsigned)sizeof(R) : 0u;
 #pragma unroll
-    for (int u = 0; u < UH; ++u) {
-      const int lj = hl[u] >> 8, li = hl[u] & 255;
-      ve[c][u] = in[u] ? pe[off[u]] : R(0);
-      vb[c][u] = in[u] && lj < BH && li < BW ? pb[off[u]] : R(0);
+    for (int c = 0; c < 3; ++c) {
+      cp_async_val<R>(&se[c][lj][li], S.E[cur][c] + off[u], nb);
+      if (lj < BH && li < BW)
+        cp_async_val<R>(&sb[c][lj][li], S.B[cur][c] + off[u], nb);
     }
   }
   // J on local [0, X] x [0, Y]: halo cells (li, lj) >= (1, 1)
@@ -275,16 +298,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       for (int c = 0; c < 3; ++c) sj[c][lj][li] = j_scale(S, c, vj[c][u]);
     }
   }
-#pragma unroll
-  for (int u = 0; u < UH; ++u) {
-    if (threadIdx.x + u * kThreads >= HN) continue;
-    const int lj = hl[u] >> 8, li = hl[u] & 255;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      se[c][lj][li] = ve[c][u];
-      if (lj < BH && li < BW) sb[c][lj][li] = vb[c][u];
-    }
-  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 
   const int shift = s_shift;

@@ -9,9 +9,10 @@ namespace zp {
 // Yee blocks: 32 columns x yee_rows<R>() rows per CTA of 256 threads.
 // Larger blocks make the halo a smaller share of the loads and spread each
 // block's fixed work over more cells: on a 2048^2 grid 0.16 ms per Yee step
-// with 32 x 8, 0.13 ms with 32 x 16, 0.11 ms with 32 x 32 (FP32, at most 85
-// registers for three resident CTAs).  FP64 stays at 32 x 16, whose tiles
-// fill the 48 KB of static shared memory.
+// with 32 x 8, 0.13 ms with 32 x 16, 0.11 ms with 32 x 32 (FP32), 0.10 ms
+// once the E and B halo goes straight into shared memory and four CTAs fit
+// per SM.  FP64 stays at 32 x 16, whose tiles fill the 48 KB of static
+// shared memory.
 constexpr int kYeeX = 32;
 constexpr int kYeeY = 16;
 template <typename R>
