@@ -393,7 +393,9 @@ __global__ void __launch_bounds__(kThreads, kYeeCtas)
 // block (32 x Y): J on [-2, 34) x [-2, Y+2) in shared memory, the two x
 // passes on all Y+4 rows, the two y passes on the block's rows; with an open x boundary
 // every pass reads zero outside [0, nx), as if each pass were a separate
-// sweep over the grid.  Writes Jf, which the Yee kernel then reads.
+// sweep over the grid.  Writes Jf, which the Yee kernel then reads.  The
+// three components' halos are loaded together (every load issued before
+// the first is used), so a block waits for one memory round trip.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     filter_kernel(const SimDev<R> *__restrict__ sims,
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int X = kYeeX, Y = yee_rows<R>();
   constexpr int W = X + 4, H = Y + 4;
   static_assert(X * Y % kThreads == 0, "whole output cells per thread");
-  __shared__ R a[H][W];       // J, then the compensated x pass
+  __shared__ R a3[3][H][W];   // J per component, then its compensated x pass
   __shared__ R b[H][W];       // binomial x pass, then binomial y pass
   const int step = st->step;
   if (frozen(st, step)) return;
@@ -412,12 +414,46 @@ __global__ void __launch_bounds__(kThreads)
   const int cur = step & 1;
   const bool open_x = S.open_x != 0;
   const R q = R(0.25), h = R(0.5), c15 = R(1.5);
-  for (int c = 0; c < 3; ++c) {
-    for (int k = threadIdx.x; k < H * W; k += blockDim.x) {
+  {
+    constexpr int HN = H * W;
+    constexpr int UF = (HN + kThreads - 1) / kThreads;
+    const int nx = S.nx, ny = S.ny;
+    size_t off[UF];
+    bool in[UF];  // a halo cell, and not beyond an open x edge
+#pragma unroll
+    for (int u = 0; u < UF; ++u) {
+      const int k = threadIdx.x + u * kThreads;
       const int lj = k / W, li = k - lj * W;
-      a[lj][li] = fld_j(S, cur, c, x0 - 2 + li, y0 - 2 + lj);
+      int gi = x0 - 2 + li;
+      const int gj = wrapg(y0 - 2 + lj, ny);
+      bool ok = k < HN;
+      if (open_x)
+        ok = ok && gi >= 0 && gi < nx;
+      else
+        gi = wrapg(gi, nx);
+      in[u] = ok;
+      off[u] = (size_t)gj * S.ld + (ok ? gi : 0);
     }
-    __syncthreads();
+    JRaw<R> v[3][UF];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const JRaw<R> *__restrict__ pj = j_plane(S, cur, c);
+#pragma unroll
+      for (int u = 0; u < UF; ++u) v[c][u] = in[u] ? pj[off[u]] : JRaw<R>(0);
+    }
+#pragma unroll
+    for (int u = 0; u < UF; ++u) {
+      const int k = threadIdx.x + u * kThreads;
+      if (k >= HN) continue;
+      const int lj = k / W, li = k - lj * W;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        a3[c][lj][li] = in[u] ? j_scale(S, c, v[c][u]) : R(0);
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) {
+    R(*a)[W] = a3[c];
     // x binomial on local columns 1..W-2 (global x0 - 1 .. x0 + X)
     for (int k = threadIdx.x; k < H * (W - 2); k += blockDim.x) {
       const int lj = k / (W - 2), li = 1 + k - lj * (W - 2);
