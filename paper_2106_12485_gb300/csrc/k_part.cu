@@ -63,6 +63,49 @@ __device__ __forceinline__ double window_density(const SpeciesDev<R> &P,
   return P.n0;
 }
 
+// One outbox entry in registers: loaded from the tile's outbox, stored to
+// slot d of the destination tile's segment (or parked in the overflow
+// buffer when d is beyond the tile's capacity).
+template <typename R>
+struct OutboxEntry {
+  int ix = 0, iy = 0, id = 0;
+  R x = R(0), y = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(1);
+  __device__ __forceinline__ void load(const SpeciesDev<R> &P, size_t e,
+                                       bool has_w, bool has_id) {
+    ix = P.ob_ix[e];
+    iy = P.ob_iy[e];
+    x = P.ob_x[e];
+    y = P.ob_y[e];
+    ux = P.ob_ux[e];
+    uy = P.ob_uy[e];
+    uz = P.ob_uz[e];
+    if (has_w) w = P.ob_w[e];
+    if (has_id) id = P.ob_id[e];
+  }
+  __device__ __forceinline__ void store(const Planes<R> &O,
+                                        const SpeciesDev<R> &P,
+                                        OverflowDev<R> &ovf,
+                                        BatchStatus *st, int step, int sim,
+                                        int s, int dest, int ntx, int tx,
+                                        int ty, int d, int cap, int off,
+                                        bool has_w, bool has_id) const {
+    if (d < cap) {
+      const size_t t = (size_t)off + d;
+      const int dx0 = (dest % ntx) * tx, dy0 = (dest / ntx) * ty;
+      O.cell[t] = local_cell(ix - dx0, iy - dy0);
+      O.x[t] = x;
+      O.y[t] = y;
+      O.ux[t] = ux;
+      O.uy[t] = uy;
+      O.uz[t] = uz;
+      if (has_w) O.w[t] = w;
+      if (has_id) O.id[t] = id;
+    } else {
+      park(ovf, st, step, sim, s, ix, iy, id, x, y, ux, uy, uz, w);
+    }
+  }
+};
+
 constexpr int kPT_MIG = 128;
 constexpr int kWarpsMig = kPT_MIG / 32;  // tiles per CTA
 
@@ -122,46 +165,37 @@ __global__ void __launch_bounds__(kPT_MIG)
     const bool has_w = O.w != nullptr, has_id = O.id != nullptr;
     const int n_out = P.ob_cnt[tile];
     const size_t ob0 = (size_t)tile * P.ob_cap;
+    // one group of 32 entries per pass; the next group's entries are loaded
+    // while this one claims its slots, and the destination's count,
+    // capacity and offset (which no lane changes here) before the claim, so
+    // a pass waits for about one memory round trip
+    OutboxEntry<R> cur;
+    bool mine = lane < n_out;
+    if (mine) cur.load(P, ob0 + lane, has_w, has_id);
     for (int k0 = 0; k0 < n_out; k0 += 32) {
-      const int k = k0 + lane;
-      const bool mine = k < n_out;
-      int ix = 0, iy = 0, id = 0, dest = 0;
-      R x = R(0), y = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(1);
+      OutboxEntry<R> nxt;
+      const bool mine_n = k0 + 32 + lane < n_out;
+      if (mine_n) nxt.load(P, ob0 + k0 + 32 + lane, has_w, has_id);
+      const int ix = cur.ix, iy = cur.iy;
+      const int dest = mine ? (iy / ty) * ntx + ix / tx : 0;
+      int cnt_d = 0, cap_d = 0, off_d = 0;
       if (mine) {
-        const size_t e = ob0 + k;
-        ix = P.ob_ix[e];
-        iy = P.ob_iy[e];
-        x = P.ob_x[e];
-        y = P.ob_y[e];
-        ux = P.ob_ux[e];
-        uy = P.ob_uy[e];
-        uz = P.ob_uz[e];
-        if (has_w) w = P.ob_w[e];
-        if (has_id) id = P.ob_id[e];
-        dest = (iy / ty) * ntx + ix / tx;
+        cnt_d = P.cnt[dest];
+        cap_d = P.cap[dest];
+        off_d = P.off[dest];
       }
       // lanes without an entry get keys of their own
       const unsigned peers = __match_any_sync(kAll, mine ? dest : -1 - lane);
-      if (!mine) continue;
-      const int leader = __ffs(peers) - 1;
-      int slot = 0;
-      if (lane == leader) slot = atomicAdd(P.arr + dest, __popc(peers));
-      slot = __shfl_sync(peers, slot, leader) + __popc(peers & lt);
-      const int d = P.cnt[dest] + slot;
-      if (d < P.cap[dest]) {
-        const size_t t = (size_t)P.off[dest] + d;
-        const int dx0 = (dest % ntx) * tx, dy0 = (dest / ntx) * ty;
-        O.cell[t] = local_cell(ix - dx0, iy - dy0);
-        O.x[t] = x;
-        O.y[t] = y;
-        O.ux[t] = ux;
-        O.uy[t] = uy;
-        O.uz[t] = uz;
-        if (has_w) O.w[t] = w;
-        if (has_id) O.id[t] = id;
-      } else {
-        park(ovf, st, step, it.x, s, ix, iy, id, x, y, ux, uy, uz, w);
+      if (mine) {
+        const int leader = __ffs(peers) - 1;
+        int slot = 0;
+        if (lane == leader) slot = atomicAdd(P.arr + dest, __popc(peers));
+        slot = __shfl_sync(peers, slot, leader) + __popc(peers & lt);
+        cur.store(O, P, ovf, st, step, it.x, s, dest, ntx, tx, ty,
+                  cnt_d + slot, cap_d, off_d, has_w, has_id);
       }
+      cur = nxt;
+      mine = mine_n;
     }
     // moving window: cold plasma on a lattice enters through column nx-1
     if (inject_col && P.inj_ppc_x > 0) {
