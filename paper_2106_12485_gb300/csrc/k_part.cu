@@ -388,12 +388,12 @@ cudaError_t launch_init_load(const SimDev<R> *sim_dev, int ntiles,
 // access is coalesced whatever the permutation.  The first plane's copy
 // runs while the rank tables are built, and each later one while the plane
 // before it is written out (into a second buffer laid over the tables and
-// the cells, when a plane fits there: always in FP32).  The particles of one cell then take their
-// ranks in any order.  Larger ones are moved particle by particle, kSortU
-// chunks of slots per memory round trip, the chunks taking their ranks one
-// after the other so that a store close to the sorted order is rewritten in
-// long runs.  A tile whose rank table exceeds the shared-memory budget keeps
-// its order.
+// the cells, when a plane fits there: always in FP32).  The particles of
+// one cell then take their ranks in any order.  Larger ones are moved
+// particle by particle, kSortU chunks of slots per memory round trip, the
+// chunks taking their ranks one after the other so that a store close to
+// the sorted order is rewritten in long runs.  A tile whose rank table
+// exceeds the shared-memory budget keeps its order.
 constexpr int kSortThreads = 512;
 constexpr int kSortMaxCells = 1024;   // tiles up to 32 x 32
 constexpr int kSortMaskWords = 6144;  // ranks x 32-cell words
@@ -409,7 +409,8 @@ __host__ __device__ constexpr size_t sort_tables_bytes() {
 }
 template <typename R>
 size_t sort_smem_bytes() {
-  // tables, then cells and permutation (16-bit slots), then one plane
+  // tables, then cells and permutation (16-bit slots), then one plane (the
+  // second plane buffer lies over the tables and the cells)
   return sort_tables_bytes() + 4 * (size_t)kSortStaged<R> +
          sizeof(R) * (size_t)kSortStaged<R>;
 }
